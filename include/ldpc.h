@@ -1,0 +1,158 @@
+/*
+ * ldpc.h - C ABI of the GB300 (sm_103a) LDPC belief-propagation decoding library.
+ *
+ * The library decodes many codewords of a quasi-cyclic LDPC code at once on one GPU:
+ * check-node update, variable-node update, a-posteriori LLR sum, hard decision and
+ * syndrome early exit (Amiri & Mehrpouyan, arXiv 1812.06545: Sec. II decoding
+ * algorithms, Algorithm 1 loop order; Sec. III-A frame-level parallelism over F frames;
+ * Sec. III-B interleaving of frames; Sec. III-C concurrent streams).
+ *
+ * Conventions shared by every entry point
+ *   - LLR sign: L = ln P(c = 0) / P(c = 1); BPSK maps bit 0 to +1.  Hard decision
+ *     c = [APP < 0] (an APP of exactly zero decodes to 0).
+ *   - User layouts are row-major per codeword: llr[n_cw][N], bits[n_cw][N] (one byte per
+ *     bit, values 0/1), iters[n_cw], app[n_cw][N].
+ *   - Device pointers are CUDA device (or managed) memory owned by the caller; host
+ *     pointers are host memory owned by the caller (pinned memory lets copies overlap).
+ *   - Decoding is asynchronous on the caller's CUDA stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream).  Argument errors are reported synchronously
+ *     before anything is launched; CUDA launch errors return LDPC_ECUDA.
+ *   - The library owns ldpc_code objects and its own internal buffers; nothing the
+ *     caller passes in is retained after a call returns (except inside the stream's
+ *     queued work, which the caller must keep alive until the stream reaches it).
+ *   - No C++ exception crosses this interface.  ldpc_last_error() returns a message for
+ *     the calling thread's most recent failure.
+ */
+#ifndef LDPC_GB300_H
+#define LDPC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LDPC_OK = 0,
+    LDPC_EINVAL = -1,    /* bad argument: null pointer, bad size, bad code, bad params  */
+    LDPC_ENOMEM = -2,    /* host or device allocation failed, or workspace too small    */
+    LDPC_ECUDA = -3,     /* a CUDA call or launch failed                                */
+    LDPC_EBUSY = -4,     /* resource in use                                             */
+    LDPC_ETIMEDOUT = -5, /* a bounded wait ran out                                      */
+    LDPC_ENOTSUP = -6    /* combination not supported (e.g. code too large for a form)  */
+} ldpc_status;
+
+typedef enum { LDPC_SCHED_FLOODING = 0, LDPC_SCHED_LAYERED = 1 } ldpc_schedule;
+typedef enum { LDPC_ALGO_SPA = 0, LDPC_ALGO_NMS = 1 } ldpc_algo;
+typedef enum { LDPC_MSG_F32 = 0, LDPC_MSG_F16 = 1, LDPC_MSG_I8 = 2 } ldpc_msg_type;
+typedef enum { LDPC_LLR_F32 = 0, LDPC_LLR_I8 = 1 } ldpc_llr_type;
+typedef enum {
+    LDPC_IMPL_AUTO = 0,  /* the optimised kernels for the requested form                */
+    LDPC_IMPL_PLAIN = 1  /* the plain FP32 flooding comparator (one codeword per thread, */
+                         /* library expm1f/log1pf phi, no early-exit skipping)           */
+} ldpc_impl;
+
+/* Opaque code object (library-owned, immutable after creation, usable from any thread). */
+typedef struct ldpc_code ldpc_code;
+
+/* Decoder parameters.  Supported forms:
+ *   sched FLOODING + algo SPA + msg F32 or F16  (sum-product, messages stored in HBM)
+ *   sched LAYERED  + algo NMS + msg I8          (bit-exact integer normalised min-sum)
+ * Every field must be set; ldpc_default_params() fills the defaults below. */
+typedef struct {
+    int32_t sched;           /* ldpc_schedule; default FLOODING                               */
+    int32_t algo;            /* ldpc_algo; default SPA                                        */
+    int32_t msg;             /* ldpc_msg_type; default F32                                    */
+    int32_t max_iter;        /* >= 1; default 20                                              */
+    int32_t early_exit;      /* 0/1: stop a codeword once H.c = 0 after an iteration (1)      */
+    float phi_clamp;         /* X > 1: |Q| is clamped to [phi(X), X] before phi (80.0)        */
+    int32_t nms_alpha_num;   /* min-sum scaling (alpha_num * mag) >> alpha_shift (3)          */
+    int32_t nms_alpha_shift; /* (2): alpha = 0.75                                             */
+    int32_t msg_sat;         /* min-sum message saturation, 1..127 (31)                       */
+    int32_t app_sat;         /* min-sum posterior saturation, msg_sat..127 (127)              */
+    float llr_scale;         /* fp32 LLR quantiser q = sat(rint(llr_scale * L)) (2.0)         */
+    int32_t impl;            /* ldpc_impl (AUTO)                                              */
+    int32_t reserved[4];     /* must be zero                                                  */
+} ldpc_decode_params;
+
+/* Fill *p with the defaults listed above.  Returns LDPC_EINVAL if p is NULL. */
+ldpc_status ldpc_default_params(ldpc_decode_params *p);
+
+/* Create a code from a QC base matrix (Sec. II, Eq. 1 gives H as an edge set between
+ * check and variable nodes; the quasi-cyclic lifting defines H block by block).
+ *   base  host pointer, row-major int32 [mb][nb], copied; entry -1 = zero block, entry
+ *         s in [0, Z) = Z x Z identity shifted so that row r has its one in column
+ *         (r + s) mod Z.  Check l*Z + r therefore joins variable j*Z + (r + s_lj) mod Z.
+ *   Limits: 1 <= mb < nb, mb <= 64, nb <= 128, 1 <= Z <= 1024, nonzero blocks <= 1024,
+ *   every block row holds >= 2 nonzero blocks, every block column >= 1.
+ * Returns LDPC_EINVAL on a bad matrix (shift out of range, empty row, mb >= nb), LDPC_ENOMEM
+ * or LDPC_ECUDA if the device tables cannot be created.  *out is set only on success. */
+ldpc_status ldpc_code_create(const int32_t *base, int32_t mb, int32_t nb, int32_t Z, ldpc_code **out);
+
+/* Destroy a code (NULL is ignored).  Work already queued with it must have completed. */
+void ldpc_code_destroy(ldpc_code *code);
+
+/* Query sizes: N = nb*Z variables, K = N - M, M = mb*Z checks, E = edges.  Any output
+ * pointer may be NULL. */
+ldpc_status ldpc_code_info(const ldpc_code *code, int32_t *N, int32_t *K, int32_t *M, int64_t *E);
+
+/* Device workspace needed by ldpc_decode_batch for n_cw codewords with these params. */
+ldpc_status ldpc_workspace_size(const ldpc_code *code, const ldpc_decode_params *p, int64_t n_cw,
+                                size_t *bytes);
+
+/* Decode n_cw codewords (Sec. II: Algorithm 1 loop order for the flooding schedule,
+ * "Algorithm 2" for the layered schedule; Sec. III-A: all codewords in parallel).
+ *   llr_dev    device, [n_cw][N], fp32 (LDPC_LLR_F32) or int8 already quantised to
+ *              [-msg_sat, msg_sat] (LDPC_LLR_I8, layered NMS only).  fp32 input to the
+ *              layered NMS form is quantised with p->llr_scale inside the library.
+ *   bits_dev   device, [n_cw][N] uint8 0/1 hard decisions after the last iteration run.
+ *   iters_dev  device, [n_cw] int32: iterations run (1..max_iter).
+ *   app_dev    device, [n_cw][N] fp32 posterior LLRs after the last iteration, or NULL
+ *              (integer forms write their integer APP converted exactly to fp32).
+ *   workspace  device scratch of >= ldpc_workspace_size() bytes, 256-byte aligned, or NULL
+ *              to let the library allocate and free it stream-ordered on `stream`.
+ * n_cw == 0 returns LDPC_OK with nothing launched. */
+ldpc_status ldpc_decode_batch(const ldpc_code *code, const ldpc_decode_params *p,
+                              const void *llr_dev, int32_t llr_type, int64_t n_cw,
+                              uint8_t *bits_dev, int32_t *iters_dev, float *app_dev,
+                              void *workspace, size_t workspace_bytes, void *stream);
+
+/* Multi-stream host-to-host decoding (Sec. III-C: W streams, each decoding its own set
+ * of frames so that copies and kernels of different sets overlap).
+ *   llr_host   host, [n_cw][N] fp32 (pinned memory recommended).
+ *   bits_host  host, [n_cw][N] uint8;  iters_host host [n_cw] int32 (may be NULL).
+ *   n_streams  W >= 1; the batch is cut into chunks of at most chunk_cw codewords
+ *              (chunk_cw <= 0: n_cw / W rounded up) issued round-robin over W internal
+ *              streams, each chunk being H2D copy -> decode -> D2H copy on its stream.
+ * Blocks until every chunk has finished.  Device buffers are owned by the library and
+ * kept for reuse between calls on the same thread. */
+ldpc_status ldpc_decode_host(const ldpc_code *code, const ldpc_decode_params *p, const float *llr_host,
+                             int64_t n_cw, uint8_t *bits_host, int32_t *iters_host, int32_t n_streams,
+                             int64_t chunk_cw);
+
+/* Release the device buffers and streams ldpc_decode_host keeps for the calling thread. */
+void ldpc_release_host_buffers(void);
+
+/* Per-kernel timing: when enabled, every kernel the library launches is bracketed by CUDA
+ * events on its launch stream; ldpc_profile_read returns, per kernel family, the number
+ * of launches and the summed event time in milliseconds (it synchronizes the pending
+ * events).  Families: 0 interleave, 1 check-node, 2 variable-node, 3 deinterleave,
+ * 4 layered, 5 plain check-node, 6 plain variable-node. */
+ldpc_status ldpc_profile_enable(int32_t on);
+ldpc_status ldpc_profile_read(int32_t family, int64_t *launches, double *ms);
+ldpc_status ldpc_profile_reset(void);
+
+/* Number of kernel launches the library has issued since the last reset (all families). */
+int64_t ldpc_launch_count(void);
+void ldpc_launch_count_reset(void);
+
+/* Message for the calling thread's most recent failure ("" if none).  Valid until the
+ * thread's next call into the library. */
+const char *ldpc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDPC_GB300_H */

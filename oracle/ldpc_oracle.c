@@ -222,10 +222,11 @@ static int check_csr(int M, int N, const int32_t *rp, const int32_t *ci)
  *   Without convergence iters = max_iter and the output is the last hard decision.
  *
  * L: fp32 [B][N] (the same array the GPU decodes); outputs app [B][N] (may be NULL),
- * bits [B][N], iters [B]. */
+ * bits [B][N], iters [B], and the last check-to-variable messages R [B][E] in CSR edge
+ * order (may be NULL). */
 int orc_spa_flood(int M, int N, const int32_t *rp, const int32_t *ci,
                   const float *L, int64_t B, int max_iter, int early_exit, double X, int fp16_msgs,
-                  double *app_out, uint8_t *bits_out, int32_t *iters_out, int nthreads)
+                  double *app_out, uint8_t *bits_out, int32_t *iters_out, double *R_out, int nthreads)
 {
     if (max_iter < 1 || !(X > 1.0) || check_csr(M, N, rp, ci) != ORC_OK) return ORC_EINVAL;
     const int E = rp[M];
@@ -295,6 +296,8 @@ int orc_spa_flood(int M, int N, const int32_t *rp, const int32_t *ci,
                 if (app_out)
                     for (int n = 0; n < N; n++) app_out[b * (int64_t)N + n] = app[n];
                 for (int n = 0; n < N; n++) bits_out[b * (int64_t)N + n] = hd[n];
+                if (R_out)
+                    for (int e = 0; e < E; e++) R_out[b * (int64_t)E + e] = R[e];
                 iters_out[b] = iters;
             }
         }

@@ -1,0 +1,223 @@
+// Horizontal layered normalised min-sum in saturated 8-bit arithmetic on sm_103a
+// (Sec. II "Algorithm 2": the checks of a layer are computed from the current variable
+// values and those values are updated at once; Sec. III-A frame-level parallelism).
+//
+// One CTA decodes C codewords from start to finish with all decoder state on chip:
+// posterior APP int8 [C][N] and check-to-variable messages R int8 [C][E] in shared
+// memory; HBM sees only the channel LLRs in and the hard decisions / iteration counts
+// out.  Thread (c, r) owns row r of every block row (layer) of codeword c.  In a QC
+// layer the Z checks touch disjoint variables (each block is one circulant), so the Z
+// row threads of a codeword update a layer concurrently; a CTA barrier separates layers.
+//
+// Arithmetic per check, every step in int32 then saturated exactly as specified:
+//   Q_k   = sat(APP_n - R_k, msg_sat)
+//   min1  = smallest |Q|, min2 = second smallest (duplicates counted), arg = first edge
+//           attaining min1 (if two edges tie then min2 = min1 and the choice is immaterial)
+//   S     = XOR of the signs [Q_k < 0]
+//   R_k   = +-((alpha_num * (k == arg ? min2 : min1)) >> alpha_shift), negative iff
+//           S xor [Q_k < 0]
+//   APP_n = sat(Q_k + R_k, app_sat)
+// After every iteration the hard decisions [APP < 0] are checked against all checks; a
+// codeword with zero syndrome stops and reports that iteration (early exit).
+#include "ldpc_internal.h"
+
+namespace ldpc {
+
+__device__ __forceinline__ int sat_i(int x, int s) { return max(-s, min(s, x)); }
+
+struct LayeredArgs {
+    const void *llr;
+    int llr_type;
+    float scale;
+    int64_t n_cw;
+    int C;
+    int max_iter, early_exit, alpha_num, alpha_shift, msg_sat, app_sat;
+    uint8_t *bits;
+    int32_t *iters;
+    float *app_out;
+};
+
+template <int DMAX>
+__global__ void __launch_bounds__(512) k_layered_nms(const CodeDev *__restrict__ cd, LayeredArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = cd->N, E = cd->E, Z = cd->Z, mb = cd->mb;
+    const int C = a.C;
+    const int strideA = (N + 15) & ~15, strideR = (E + 15) & ~15;
+    int8_t *APP = reinterpret_cast<int8_t *>(smem);
+    int8_t *Rm = APP + (size_t)C * strideA;
+    int *flag = reinterpret_cast<int *>(Rm + (size_t)C * strideR);  // [C] syndrome failure flags
+    int *active = flag + C;                                          // [C] 1 while decoding
+    int *its = active + C;                                           // [C] iterations run
+    const int64_t cw0 = (int64_t)blockIdx.x * C;
+    const int tid = threadIdx.x, nth = blockDim.x;
+
+    // load + quantise the channel LLRs, clear the messages
+    for (int i = tid; i < C * N; i += nth) {
+        const int c = i / N, n = i - c * N;
+        const int64_t cw = cw0 + c;
+        int q = 0;
+        if (cw < a.n_cw) {
+            if (a.llr_type == LDPC_LLR_I8) {
+                q = sat_i(static_cast<const int8_t *>(a.llr)[cw * N + n], a.msg_sat);
+            } else {
+                const float p = __fmul_rn(a.scale, static_cast<const float *>(a.llr)[cw * N + n]);
+                const float rr = rintf(p);
+                q = rr > (float)a.msg_sat ? a.msg_sat : (rr < -(float)a.msg_sat ? -a.msg_sat : (int)rr);
+            }
+        }
+        APP[c * strideA + n] = (int8_t)q;
+    }
+    for (int i = tid; i < C * strideR / 4; i += nth) reinterpret_cast<int *>(Rm)[i] = 0;
+    for (int c = tid; c < C; c += nth) {
+        flag[c] = 0;
+        active[c] = (cw0 + c) < a.n_cw ? 1 : 0;
+        its[c] = a.max_iter;
+    }
+    __syncthreads();
+
+    const int c = tid / Z, r = tid - (tid / Z) * Z;
+    const bool mine = c < C;
+    int8_t *A = APP + (mine ? c : 0) * strideA;
+    int8_t *Rc = Rm + (mine ? c : 0) * strideR;
+
+    for (int t = 1; t <= a.max_iter; t++) {
+        for (int l = 0; l < mb; l++) {
+            const int b0 = cd->rowptr[l], dc = cd->rowptr[l + 1] - b0;
+            if (mine && active[c]) {
+                int q[DMAX];
+                int min1 = 0x7fffffff, min2 = 0x7fffffff, arg = -1;
+                unsigned S = 0;
+#pragma unroll
+                for (int k = 0; k < DMAX; k++) {
+                    if (k < dc) {
+                        const int ent = cd->ent[b0 + k];
+                        int x = r + (ent & 0xffff);
+                        x -= (x >= Z) ? Z : 0;
+                        const int n = (ent >> 16) * Z + x;
+                        const int qq = sat_i((int)A[n] - (int)Rc[(b0 + k) * Z + r], a.msg_sat);
+                        const int mag = qq < 0 ? -qq : qq;
+                        if (mag < min1) {
+                            min2 = min1;
+                            min1 = mag;
+                            arg = k;
+                        } else if (mag < min2) {
+                            min2 = mag;
+                        }
+                        S ^= qq < 0 ? 1u : 0u;
+                        q[k] = qq;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < DMAX; k++) {
+                    if (k < dc) {
+                        const int ent = cd->ent[b0 + k];
+                        int x = r + (ent & 0xffff);
+                        x -= (x >= Z) ? Z : 0;
+                        const int n = (ent >> 16) * Z + x;
+                        const int mag = (k == arg) ? min2 : min1;
+                        const int magp = (a.alpha_num * mag) >> a.alpha_shift;
+                        const int rn = (S ^ (q[k] < 0 ? 1u : 0u)) ? -magp : magp;
+                        Rc[(b0 + k) * Z + r] = (int8_t)rn;
+                        A[n] = (int8_t)sat_i(q[k] + rn, a.app_sat);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (!a.early_exit) continue;
+        // syndrome of the hard decisions: thread (c, r) checks row r of every layer
+        if (mine && active[c]) {
+            unsigned bad = 0;
+            for (int l = 0; l < mb && !bad; l++) {
+                const int b0 = cd->rowptr[l], b1 = cd->rowptr[l + 1];
+                unsigned par = 0;
+                for (int b = b0; b < b1; b++) {
+                    const int ent = cd->ent[b];
+                    int x = r + (ent & 0xffff);
+                    x -= (x >= Z) ? Z : 0;
+                    par ^= A[(ent >> 16) * Z + x] < 0 ? 1u : 0u;
+                }
+                bad |= par;
+            }
+            if (bad) flag[c] = 1;
+        }
+        __syncthreads();
+        int still = 0;
+        for (int cc = 0; cc < C; cc++) still |= active[cc] && flag[cc];
+        __syncthreads();
+        if (tid < C) {
+            if (active[tid] && !flag[tid]) {
+                its[tid] = t;
+                active[tid] = 0;
+            }
+            flag[tid] = 0;
+        }
+        __syncthreads();
+        if (!still) break;
+    }
+
+    // hard decisions, posterior and iteration counts out (row-contiguous in HBM)
+    for (int i = tid; i < C * N; i += nth) {
+        const int cc = i / N, n = i - cc * N;
+        const int64_t cw = cw0 + cc;
+        if (cw >= a.n_cw) continue;
+        const int v = APP[cc * strideA + n];
+        a.bits[cw * N + n] = v < 0 ? 1 : 0;
+        if (a.app_out) a.app_out[cw * N + n] = (float)v;
+    }
+    for (int cc = tid; cc < C; cc += nth)
+        if (cw0 + cc < a.n_cw) a.iters[cw0 + cc] = its[cc];
+}
+
+static int pick_C(const CodeDev &h) { return h.Z >= 512 ? 1 : (512 / h.Z); }
+
+static size_t layered_smem(const CodeDev &h, int C)
+{
+    return (size_t)C * (((h.N + 15) & ~15) + ((h.E + 15) & ~15)) + 3 * sizeof(int) * C;
+}
+
+int layered_supported(const CodeDev &h)
+{
+    return h.Z <= 512 && h.dc_max <= 32 && layered_smem(h, 1) <= 200 * 1024;
+}
+
+template <int DMAX>
+static cudaError_t launch_layered(const CodeDev &h, const CodeDev *d, const LayeredArgs &a, cudaStream_t s)
+{
+    const size_t sm = layered_smem(h, a.C);
+    cudaError_t e = cudaFuncSetAttribute(k_layered_nms<DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int threads = ((a.C * h.Z + 31) / 32) * 32;
+    const unsigned blocks = (unsigned)((a.n_cw + a.C - 1) / a.C);
+    LaunchScope ls(F_LAYERED, s);
+    k_layered_nms<DMAX><<<blocks, threads, sm, s>>>(d, a);
+    return cudaGetLastError();
+}
+
+cudaError_t layered_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p, const void *llr,
+                           int llr_type, int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out, cudaStream_t s)
+{
+    LayeredArgs a;
+    a.llr = llr;
+    a.llr_type = llr_type;
+    a.scale = p.llr_scale;
+    a.n_cw = n_cw;
+    a.C = pick_C(h);
+    while (a.C > 1 && layered_smem(h, a.C) > 100 * 1024) a.C--;
+    a.max_iter = p.max_iter;
+    a.early_exit = p.early_exit;
+    a.alpha_num = p.nms_alpha_num;
+    a.alpha_shift = p.nms_alpha_shift;
+    a.msg_sat = p.msg_sat;
+    a.app_sat = p.app_sat;
+    a.bits = bits;
+    a.iters = iters;
+    a.app_out = app_out;
+    if (h.dc_max <= 8) return launch_layered<8>(h, d, a, s);
+    if (h.dc_max <= 16) return launch_layered<16>(h, d, a, s);
+    if (h.dc_max <= 24) return launch_layered<24>(h, d, a, s);
+    return launch_layered<32>(h, d, a, s);
+}
+
+}  // namespace ldpc

@@ -1,0 +1,436 @@
+// C ABI of the decoding library: code objects, parameter validation, workspace and
+// dispatch to the flooding / layered kernels, the multi-stream host path (Sec. III-C)
+// and per-kernel event timing.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ldpc_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+ldpc_status fail(ldpc_status st, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+ldpc_status fail(ldpc_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+ldpc_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(LDPC_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------- profiling state
+
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_prof_on{0};
+std::mutex g_prof_mu;
+struct Pending {
+    int family;
+    cudaEvent_t a, b;
+};
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_event_pool;
+int64_t g_fam_launches[ldpc::F_COUNT];
+double g_fam_ms[ldpc::F_COUNT];
+
+cudaEvent_t take_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void drain_pending()
+{
+    for (auto &p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            g_fam_launches[p.family]++;
+            g_fam_ms[p.family] += ms;
+        }
+        g_event_pool.push_back(p.a);
+        g_event_pool.push_back(p.b);
+    }
+    g_pending.clear();
+}
+
+}  // namespace
+
+namespace ldpc {
+
+LaunchScope::LaunchScope(int fam, cudaStream_t s) : family(fam), stream(s), on(false)
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_prof_on.load(std::memory_order_relaxed)) {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        ev[0] = take_event();
+        ev[1] = take_event();
+        if (ev[0] && ev[1] && cudaEventRecord(ev[0], s) == cudaSuccess) on = true;
+    }
+}
+
+LaunchScope::~LaunchScope()
+{
+    if (!on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (cudaEventRecord(ev[1], stream) == cudaSuccess) g_pending.push_back({family, ev[0], ev[1]});
+    if (g_pending.size() > 4096) drain_pending();
+}
+
+}  // namespace ldpc
+
+using ldpc::CodeDev;
+
+extern "C" {
+
+const char *ldpc_last_error(void) { return g_err.c_str(); }
+
+ldpc_status ldpc_default_params(ldpc_decode_params *p)
+{
+    if (!p) return fail(LDPC_EINVAL, "params is NULL");
+    memset(p, 0, sizeof *p);
+    p->sched = LDPC_SCHED_FLOODING;
+    p->algo = LDPC_ALGO_SPA;
+    p->msg = LDPC_MSG_F32;
+    p->max_iter = 20;
+    p->early_exit = 1;
+    p->phi_clamp = 80.0f;
+    p->nms_alpha_num = 3;
+    p->nms_alpha_shift = 2;
+    p->msg_sat = 31;
+    p->app_sat = 127;
+    p->llr_scale = 2.0f;
+    p->impl = LDPC_IMPL_AUTO;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_code_create(const int32_t *base, int32_t mb, int32_t nb, int32_t Z, ldpc_code **out)
+{
+    if (!base || !out) return fail(LDPC_EINVAL, "base or out is NULL");
+    if (mb < 1 || nb <= mb || mb > ldpc::MB_MAX || nb > ldpc::NB_MAX)
+        return fail(LDPC_EINVAL, "need 1 <= mb < nb, mb <= %d, nb <= %d (got %d x %d)", ldpc::MB_MAX, ldpc::NB_MAX,
+                    mb, nb);
+    if (Z < 1 || Z > ldpc::Z_MAX) return fail(LDPC_EINVAL, "Z must be in [1, %d] (got %d)", ldpc::Z_MAX, Z);
+    ldpc_code *c = new (std::nothrow) ldpc_code;
+    if (!c) return fail(LDPC_ENOMEM, "host allocation failed");
+    memset(&c->host, 0, sizeof c->host);
+    CodeDev &h = c->host;
+    h.mb = mb;
+    h.nb = nb;
+    h.Z = Z;
+    int nnz = 0;
+    std::vector<int> coldeg(nb, 0);
+    for (int l = 0; l < mb; l++) {
+        h.rowptr[l] = nnz;
+        int deg = 0;
+        for (int j = 0; j < nb; j++) {
+            const int s = base[l * nb + j];
+            if (s < -1 || s >= Z) {
+                delete c;
+                return fail(LDPC_EINVAL, "base[%d][%d] = %d outside [-1, Z=%d)", l, j, s, Z);
+            }
+            if (s < 0) continue;
+            if (nnz >= ldpc::NNZ_MAX) {
+                delete c;
+                return fail(LDPC_EINVAL, "more than %d nonzero blocks", ldpc::NNZ_MAX);
+            }
+            h.ent[nnz++] = (j << 16) | s;
+            deg++;
+            coldeg[j]++;
+        }
+        if (deg < 2) {
+            delete c;
+            return fail(LDPC_EINVAL, "block row %d has %d nonzero blocks (need >= 2)", l, deg);
+        }
+        if (deg > h.dc_max) h.dc_max = deg;
+    }
+    h.rowptr[mb] = nnz;
+    int k = 0;
+    for (int j = 0; j < nb; j++) {
+        if (coldeg[j] < 1) {
+            delete c;
+            return fail(LDPC_EINVAL, "block column %d is empty", j);
+        }
+        if (coldeg[j] > h.dv_max) h.dv_max = coldeg[j];
+        h.colptr[j] = k;
+        for (int b = 0; b < nnz; b++)
+            if ((h.ent[b] >> 16) == j) h.colent[k++] = (b << 16) | (h.ent[b] & 0xffff);
+    }
+    h.colptr[nb] = k;
+    h.nnz = nnz;
+    h.N = nb * Z;
+    h.M = mb * Z;
+    h.K = h.N - h.M;
+    h.E = nnz * Z;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->dev, sizeof(CodeDev));
+    if (e == cudaSuccess) e = cudaMemcpy(c->dev, &h, sizeof(CodeDev), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "device code tables");
+    }
+    *out = c;
+    return LDPC_OK;
+}
+
+void ldpc_code_destroy(ldpc_code *c)
+{
+    if (!c) return;
+    if (c->dev) cudaFree(c->dev);
+    delete c;
+}
+
+ldpc_status ldpc_code_info(const ldpc_code *c, int32_t *N, int32_t *K, int32_t *M, int64_t *E)
+{
+    if (!c) return fail(LDPC_EINVAL, "code is NULL");
+    if (N) *N = c->host.N;
+    if (K) *K = c->host.K;
+    if (M) *M = c->host.M;
+    if (E) *E = c->host.E;
+    return LDPC_OK;
+}
+
+static ldpc_status check_params(const ldpc_code *c, const ldpc_decode_params *p, int llr_type)
+{
+    if (!c || !p) return fail(LDPC_EINVAL, "code or params is NULL");
+    if (p->max_iter < 1 || p->max_iter > 10000) return fail(LDPC_EINVAL, "max_iter must be in [1, 10000]");
+    if (p->early_exit != 0 && p->early_exit != 1) return fail(LDPC_EINVAL, "early_exit must be 0 or 1");
+    for (int i = 0; i < 4; i++)
+        if (p->reserved[i] != 0) return fail(LDPC_EINVAL, "reserved fields must be zero");
+    if (p->impl != LDPC_IMPL_AUTO && p->impl != LDPC_IMPL_PLAIN) return fail(LDPC_EINVAL, "bad impl");
+    if (p->sched == LDPC_SCHED_FLOODING && p->algo == LDPC_ALGO_SPA) {
+        if (p->msg != LDPC_MSG_F32 && p->msg != LDPC_MSG_F16)
+            return fail(LDPC_ENOTSUP, "flooding SPA stores messages as F32 or F16");
+        if (!(p->phi_clamp > 1.0f) || !(p->phi_clamp <= 87.0f))
+            return fail(LDPC_EINVAL, "phi_clamp must be in (1, 87] so that phi(X) is a normal fp32 value");
+        if (llr_type != LDPC_LLR_F32) return fail(LDPC_EINVAL, "flooding SPA takes fp32 LLRs");
+        if (p->impl == LDPC_IMPL_PLAIN && p->msg != LDPC_MSG_F32)
+            return fail(LDPC_ENOTSUP, "the plain comparator stores F32 messages");
+        if (c->host.dc_max > 32) return fail(LDPC_ENOTSUP, "check degree %d > 32", c->host.dc_max);
+        return LDPC_OK;
+    }
+    if (p->sched == LDPC_SCHED_LAYERED && p->algo == LDPC_ALGO_NMS) {
+        if (p->msg != LDPC_MSG_I8) return fail(LDPC_ENOTSUP, "layered min-sum stores I8 messages");
+        if (p->impl != LDPC_IMPL_AUTO) return fail(LDPC_ENOTSUP, "no plain layered implementation");
+        if (p->msg_sat < 1 || p->msg_sat > 127 || p->app_sat < p->msg_sat || p->app_sat > 127)
+            return fail(LDPC_EINVAL, "need 1 <= msg_sat <= app_sat <= 127");
+        if (p->nms_alpha_num < 1 || p->nms_alpha_shift < 0 || p->nms_alpha_shift > 16 ||
+            ((int64_t)p->nms_alpha_num * p->msg_sat >> p->nms_alpha_shift) > 127)
+            return fail(LDPC_EINVAL, "min-sum scaling must keep |R| <= 127");
+        if (llr_type == LDPC_LLR_F32 && !(p->llr_scale > 0.0f && isfinite(p->llr_scale)))
+            return fail(LDPC_EINVAL, "llr_scale must be positive");
+        if (llr_type != LDPC_LLR_F32 && llr_type != LDPC_LLR_I8) return fail(LDPC_EINVAL, "bad llr_type");
+        if (!ldpc::layered_supported(c->host))
+            return fail(LDPC_ENOTSUP, "code too large for on-chip layered decoding (Z=%d, dc_max=%d)", c->host.Z,
+                        c->host.dc_max);
+        return LDPC_OK;
+    }
+    return fail(LDPC_ENOTSUP, "unsupported sched/algo combination (%d, %d)", p->sched, p->algo);
+}
+
+static size_t ws_bytes(const ldpc_code *c, const ldpc_decode_params *p, int64_t n_cw)
+{
+    if (p->sched == LDPC_SCHED_LAYERED || n_cw == 0) return 0;
+    return ldpc::flood_ws_layout(c->host, n_cw, p->msg, nullptr, nullptr);
+}
+
+ldpc_status ldpc_workspace_size(const ldpc_code *c, const ldpc_decode_params *p, int64_t n_cw, size_t *bytes)
+{
+    if (!bytes) return fail(LDPC_EINVAL, "bytes is NULL");
+    ldpc_status st = check_params(c, p, p && p->sched == LDPC_SCHED_LAYERED ? LDPC_LLR_I8 : LDPC_LLR_F32);
+    if (st != LDPC_OK) return st;
+    if (n_cw < 0) return fail(LDPC_EINVAL, "n_cw < 0");
+    *bytes = ws_bytes(c, p, n_cw);
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_decode_batch(const ldpc_code *c, const ldpc_decode_params *p, const void *llr, int32_t llr_type,
+                              int64_t n_cw, uint8_t *bits, int32_t *iters, float *app, void *workspace,
+                              size_t workspace_bytes, void *stream)
+{
+    ldpc_status st = check_params(c, p, llr_type);
+    if (st != LDPC_OK) return st;
+    if (n_cw < 0 || n_cw > ((int64_t)1 << 31)) return fail(LDPC_EINVAL, "n_cw must be in [0, 2^31]");
+    if (n_cw == 0) return LDPC_OK;
+    if (!llr || !bits || !iters) return fail(LDPC_EINVAL, "llr, bits and iters must be non-NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (p->sched == LDPC_SCHED_LAYERED) {
+        e = ldpc::layered_decode(c->host, c->dev, *p, llr, llr_type, n_cw, bits, iters, app, s);
+        return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "layered decode launch");
+    }
+    const size_t need = ws_bytes(c, p, n_cw);
+    void *ws = workspace;
+    bool own = false;
+    if (ws) {
+        if (workspace_bytes < need)
+            return fail(LDPC_ENOMEM, "workspace of %zu bytes < %zu needed", workspace_bytes, need);
+        if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(LDPC_EINVAL, "workspace must be 256-byte aligned");
+    } else {
+        e = cudaMallocAsync(&ws, need, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LDPC_ENOMEM, "workspace allocation of %zu bytes failed: %s", need, cudaGetErrorString(e));
+        }
+        own = true;
+    }
+    ldpc::FloodWs w;
+    ldpc::flood_ws_layout(c->host, n_cw, p->msg, &w, static_cast<char *>(ws));
+    e = ldpc::flood_decode(c->host, c->dev, *p, static_cast<const float *>(llr), n_cw, bits, iters, app, w, s);
+    if (own) {
+        cudaError_t e2 = cudaFreeAsync(ws, s);
+        if (e == cudaSuccess) e = e2;
+    }
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "flooding decode launch");
+}
+
+// ---------------------------------------------------------------- multi-stream host path
+
+namespace {
+struct HostSlot {
+    cudaStream_t s = nullptr;
+    float *llr = nullptr;
+    uint8_t *bits = nullptr;
+    int32_t *iters = nullptr;
+    void *ws = nullptr;
+    int64_t cap_cw = 0;
+    int N = 0;
+    size_t ws_cap = 0;
+    int device = -1;
+};
+thread_local std::vector<HostSlot> t_slots;
+
+void free_slot(HostSlot &h)
+{
+    if (h.llr) cudaFree(h.llr);
+    if (h.bits) cudaFree(h.bits);
+    if (h.iters) cudaFree(h.iters);
+    if (h.ws) cudaFree(h.ws);
+    if (h.s) cudaStreamDestroy(h.s);
+    h = HostSlot();
+}
+}  // namespace
+
+void ldpc_release_host_buffers(void)
+{
+    for (auto &h : t_slots) {
+        if (h.s) cudaStreamSynchronize(h.s);
+        free_slot(h);
+    }
+    t_slots.clear();
+}
+
+ldpc_status ldpc_decode_host(const ldpc_code *c, const ldpc_decode_params *p, const float *llr_host, int64_t n_cw,
+                             uint8_t *bits_host, int32_t *iters_host, int32_t W, int64_t chunk_cw)
+{
+    ldpc_status st = check_params(c, p, LDPC_LLR_F32);
+    if (st != LDPC_OK) return st;
+    if (n_cw < 0) return fail(LDPC_EINVAL, "n_cw < 0");
+    if (n_cw == 0) return LDPC_OK;
+    if (!llr_host || !bits_host) return fail(LDPC_EINVAL, "llr_host and bits_host must be non-NULL");
+    if (W < 1 || W > 64) return fail(LDPC_EINVAL, "n_streams must be in [1, 64]");
+    if (chunk_cw <= 0) chunk_cw = (n_cw + W - 1) / W;
+    const int N = c->host.N;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if ((int)t_slots.size() < W) t_slots.resize(W);
+    const size_t wsb = ws_bytes(c, p, chunk_cw);
+    for (int w = 0; w < W; w++) {
+        HostSlot &h = t_slots[w];
+        if (h.device != dev || h.cap_cw < chunk_cw || h.N < N || h.ws_cap < wsb) {
+            if (h.s) cudaStreamSynchronize(h.s);
+            free_slot(h);
+            h.device = dev;
+            cudaError_t e = cudaStreamCreateWithFlags(&h.s, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaMalloc(&h.llr, (size_t)chunk_cw * N * sizeof(float));
+            if (e == cudaSuccess) e = cudaMalloc(&h.bits, (size_t)chunk_cw * N);
+            if (e == cudaSuccess) e = cudaMalloc(&h.iters, (size_t)chunk_cw * sizeof(int32_t));
+            if (e == cudaSuccess && wsb) e = cudaMalloc(&h.ws, wsb);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                free_slot(h);
+                return fail(LDPC_ENOMEM, "multi-stream buffers: %s", cudaGetErrorString(e));
+            }
+            h.cap_cw = chunk_cw;
+            h.N = N;
+            h.ws_cap = wsb;
+        }
+    }
+    int64_t done = 0;
+    for (int64_t i = 0; done < n_cw; i++) {
+        HostSlot &h = t_slots[i % W];
+        const int64_t cnt = (n_cw - done) < chunk_cw ? (n_cw - done) : chunk_cw;
+        cudaError_t e = cudaMemcpyAsync(h.llr, llr_host + done * N, (size_t)cnt * N * sizeof(float),
+                                        cudaMemcpyHostToDevice, h.s);
+        if (e != cudaSuccess) return cuda_fail(e, "H2D copy");
+        st = ldpc_decode_batch(c, p, h.llr, LDPC_LLR_F32, cnt, h.bits, h.iters, nullptr, h.ws, h.ws_cap, h.s);
+        if (st != LDPC_OK) return st;
+        e = cudaMemcpyAsync(bits_host + done * N, h.bits, (size_t)cnt * N, cudaMemcpyDeviceToHost, h.s);
+        if (e == cudaSuccess && iters_host)
+            e = cudaMemcpyAsync(iters_host + done, h.iters, (size_t)cnt * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                h.s);
+        if (e != cudaSuccess) return cuda_fail(e, "D2H copy");
+        done += cnt;
+    }
+    for (int w = 0; w < W; w++) {
+        cudaError_t e = cudaStreamSynchronize(t_slots[w].s);
+        if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    }
+    return LDPC_OK;
+}
+
+// ---------------------------------------------------------------- profiling
+
+ldpc_status ldpc_profile_enable(int32_t on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on.store(on ? 1 : 0);
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_profile_read(int32_t family, int64_t *launches, double *ms)
+{
+    if (family < 0 || family >= ldpc::F_COUNT) return fail(LDPC_EINVAL, "bad kernel family %d", family);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    drain_pending();
+    if (launches) *launches = g_fam_launches[family];
+    if (ms) *ms = g_fam_ms[family];
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_profile_reset(void)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    drain_pending();
+    for (int i = 0; i < ldpc::F_COUNT; i++) {
+        g_fam_launches[i] = 0;
+        g_fam_ms[i] = 0.0;
+    }
+    return LDPC_OK;
+}
+
+int64_t ldpc_launch_count(void) { return g_launches.load(); }
+void ldpc_launch_count_reset(void) { g_launches.store(0); }
+
+}  // extern "C"

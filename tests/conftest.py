@@ -9,3 +9,20 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300); parity tests of the CUDA path")
     config.addinivalue_line("markers", "slow: long-running statistical test")
+
+
+import pytest  # noqa: E402
+
+
+@pytest.fixture(scope="session")
+def cuda_dev():
+    """cuda:0 with the decoding library built and loaded (GPU tests only)."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test collected without a CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    return torch.device("cuda:0")
