@@ -1,0 +1,439 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 LDPC decoder.
+
+One step = one pass of the decoding path over the FP32 flooding sum-product sweep
+workload: 7 batches of 8192 codewords of the seeded rate-1/2 QC code (N = 1944, K = 972),
+one per Eb/N0 in 1.0..2.5 dB (0.25 dB steps), early exit after at most 20 iterations:
+interleave, check-node and variable-node phases with the fused syndrome, deinterleave.
+Metric: decoded info Gbit/s (K x codewords / time).  Also timed on the same inputs: the
+FP16-message form and the plain FP32 comparator; and the int8 layered min-sum form on its
+own workload (65536 codewords of the rate-5/6 code at 4.0 dB).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank decodes its own batches (weak scaling, no data-path collective);
+timing is bracketed by a barrier and synchronize on both sides and the maximum over
+ranks is reported by rank 0 as one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "decoded info Gbit/s and p99 latency at equal FER vs plain FP32 flooding SPA, 1 GB300"
+WORKLOAD = "flood_n1944_b8192_sweep"
+LAYERED_WORKLOAD = "layered_i8_n1944_r56_b65536"
+CN_SOURCE = os.path.join(ROOT, "paper_1812_06545_gb300", "csrc", "flood_kernels.cu")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--streams", type=int, default=4, help="streams of the end-to-end host path")
+    ap.add_argument("--no-forms", action="store_true", help="time only the headline form")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ inputs
+
+def workload_frames(name: str, rank: int = 0):
+    """[(ebn0, c uint8 [n, N], L fp32 [n, N])] for a named workload (rank-offset noise seeds)."""
+    from paper_1812_06545_gb300 import inputs as I
+
+    w = I.WORKLOADS[name]
+    out = []
+    for eb, ns in zip(w.ebn0_db, w.noise_seeds):
+        B, Z, c, L = I.make_frames(w.code, w.batch, eb, w.info_seed + 1000 * rank, ns + 1000 * rank)
+        out.append((eb, c, L))
+    return w, B, Z, out
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"unavailable": "nvidia-smi not available"}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"unavailable": "no samples"}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_sample_rate(frames, code_name: str, max_iter: int, budget_s: float, threads: int = 0):
+    """Time the FP64 oracle on a bounded sample of every batch: returns (info bits/s,
+    description, cores used, frame errors, frames)."""
+    from oracle import oracle as O
+    from paper_1812_06545_gb300 import inputs as I
+
+    B, Z = I.load_code(code_name)
+    oc = O.QCCode(B, Z)
+    cores = threads or O.num_threads()
+    # calibrate on 8 codewords of the hardest batch, then size the per-batch sample
+    t0 = time.perf_counter()
+    oc.spa_flood(frames[0][2][:8], max_iter, True, nthreads=threads)
+    per_cw = max((time.perf_counter() - t0) / 8, 1e-5)
+    n = int(max(8, min(len(frames[0][2]), budget_s / (per_cw * len(frames)))))
+    t0 = time.perf_counter()
+    errs = 0
+    for eb, c, L in frames:
+        _, bits, _ = oc.spa_flood(L[:n], max_iter, True, nthreads=threads)
+        errs += int((bits != c[:n]).any(axis=1).sum())
+    dt = time.perf_counter() - t0
+    rate = n * len(frames) * oc.K / dt
+    return rate, f"first {n} codewords of each of the {len(frames)} Eb/N0 batches ({n * len(frames)} codewords)", \
+        cores, errs, n * len(frames)
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1812_06545_gb300 import inputs as I
+    from oracle import oracle as O
+
+    O.build()
+    w, B, Z, frames = workload_frames(WORKLOAD)
+    oc = O.QCCode(B, Z)
+    # size each step for ~2 s of CPU work
+    t0 = time.perf_counter()
+    oc.spa_flood(frames[0][2][:8], w.max_iter, True)
+    per_cw = max((time.perf_counter() - t0) / 8, 1e-5)
+    n = int(max(4, min(w.batch, 2.0 / (per_cw * len(frames)))))
+    for _ in range(args.warmup):
+        for eb, c, L in frames:
+            oc.spa_flood(L[:n], w.max_iter, True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for eb, c, L in frames:
+            oc.spa_flood(L[:n], w.max_iter, True)
+    dt = time.perf_counter() - t0
+    value = args.steps * n * len(frames) * oc.K / dt / 1e9
+    sample = f"first {n} codewords of each of the {len(frames)} Eb/N0 batches per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "FP64 flooding sum-product (CPU oracle)", "code": w.code,
+                       "batch": w.batch, "ebn0_db": w.ebn0_db, "max_iter": w.max_iter, "early_exit": True},
+            "cpu_baseline": {"value": value, "unit": "Gbit/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_1812_06545_gb300 import ldpc
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---------------- inputs resident in HBM before timing
+    w, B, Z, frames = workload_frames(WORKLOAD, rank)
+    code = ldpc.Code(B, Z)
+    xs = [torch.from_numpy(L).to(dev) for _, _, L in frames]
+    n_per_batch = w.batch
+    stream = torch.cuda.current_stream(dev)
+
+    def params(form):
+        return ldpc.params_for(form, max_iter=w.max_iter, early_exit=1 if w.early_exit else 0)
+
+    def run_form(form, steps, warmup, profile=False, lat=None):
+        p = params(form)
+        bits = [torch.empty((n_per_batch, code.N), dtype=torch.uint8, device=dev) for _ in xs]
+        iters = [torch.empty((n_per_batch,), dtype=torch.int32, device=dev) for _ in xs]
+        wsb = ldpc.ldpc_workspace_size(code.handle, p, n_per_batch)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+
+        def step(events=None):
+            for i, x in enumerate(xs):
+                if events is not None:
+                    events[i][0].record(stream)
+                ldpc.ldpc_decode_batch(code.handle, p, x, ldpc.LDPC_LLR_F32, n_per_batch, bits[i], iters[i], None,
+                                       ws, wsb, stream)
+                if events is not None:
+                    events[i][1].record(stream)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            ldpc.ldpc_profile_reset()
+            ldpc.ldpc_profile_enable(True)
+        ldpc.ldpc_launch_count_reset()
+        evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in xs] for _ in range(steps)] \
+            if lat is not None else None
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for k in range(steps):
+            step(evs[k] if evs else None)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        launches = ldpc.ldpc_launch_count()
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            ldpc.ldpc_profile_enable(False)
+        ms = s0.elapsed_time(s1)
+        if lat is not None:
+            lat.extend(e[0].elapsed_time(e[1]) for st in evs for e in st)
+        return ms, launches, bits, iters
+
+    # ---------------- headline: FP32 flooding sum-product
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    lat = []
+    ms, launches, bits, iters = run_form("flood_f32", args.steps, args.warmup, profile=True, lat=lat)
+    clocks = sampler.stop() if sampler else None
+    ms_max = max_over_ranks(ms)
+    units = world * args.steps * len(xs) * n_per_batch
+    value = units * code.K / (ms_max * 1e-3) / 1e9
+
+    # FER and iteration statistics of the last timed step
+    fer = {}
+    iters_np = []
+    for (eb, c, _), b, it in zip(frames, bits, iters):
+        bn = b.cpu().numpy()
+        fer[f"{eb:.2f}"] = float((bn != c).any(axis=1).mean())
+        iters_np.append(it.cpu().numpy())
+
+    # roofline of the check-node kernel: algorithmic bytes of every launch in the timed region
+    n_cn, cn_ms = ldpc.ldpc_profile_read("check_node")
+    n_vn, vn_ms = ldpc.ldpc_profile_read("variable_node")
+    N, E, T = code.N, code.E, w.max_iter
+    cn_bytes = vn_bytes = 0
+    for it in iters_np:
+        last_cn = np.where(it < T, it + 1, T)        # CN(t) runs for t <= iters + 1 (syndrome check)
+        for t in range(1, T + 1):
+            a_cn = int((last_cn >= t).sum())
+            a_vn = int((it >= t).sum())
+            cn_bytes += a_cn * (4 * N + 4 * E + (4 * E if t >= 2 else 0))
+            vn_bytes += a_vn * (4 * E + 8 * N)
+    cn_bytes *= args.steps
+    vn_bytes *= args.steps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    cn_gbs = cn_bytes / (cn_ms * 1e-3) / 1e9 if cn_ms > 0 else None
+    vn_gbs = vn_bytes / (vn_ms * 1e-3) / 1e9 if vn_ms > 0 else None
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        src_hash = hashlib.sha256(open(CN_SOURCE, "rb").read()).hexdigest()
+        ent = tr.get("k_flood_cn")
+        if ent and ent.get("source_sha256") == src_hash:
+            traffic = ent.get("bytes_per_launch_full_size")
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "kernel": "k_flood_cn (check-node phase)", "achieved": cn_gbs, "peak": hbm_peak,
+                "unit": "GB/s", "frac": (cn_gbs / hbm_peak) if cn_gbs else None, "peak_source": peak_src,
+                "traffic": traffic, "launches": n_cn, "avg_launch_ms": cn_ms / max(n_cn, 1),
+                "algorithmic_bytes_per_cw_iteration": 4 * N + 8 * E,
+                "variable_node": {"achieved": vn_gbs, "frac": (vn_gbs / hbm_peak) if vn_gbs else None,
+                                  "launches": n_vn, "avg_launch_ms": vn_ms / max(n_vn, 1),
+                                  "algorithmic_bytes_per_cw_iteration": 4 * E + 8 * N}}
+
+    line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": "flooding sum-product, FP32 messages", "code": w.code,
+                       "N": code.N, "K": code.K, "batch": n_per_batch, "ebn0_db": w.ebn0_db,
+                       "max_iter": w.max_iter, "early_exit": True, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (7 x 63.7 MB LLR batches + 178 MB messages per batch)"},
+            "latency_ms": {"what": "one 8192-codeword decode call", "p50": float(np.percentile(lat, 50)),
+                           "p99": float(np.percentile(lat, 99))},
+            "avg_iterations": float(np.mean(np.concatenate(iters_np))), "fer": fer,
+            "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
+
+    # ---------------- other forms on the same inputs
+    if not args.no_forms:
+        forms = {}
+        for form in ("flood_f16", "plain_f32"):
+            fms, fl, fb, fi = run_form(form, args.steps, args.warmup)
+            fms = max_over_ranks(fms)
+            fv = units * code.K / (fms * 1e-3) / 1e9
+            ffer = {f"{eb:.2f}": float((b.cpu().numpy() != c).any(axis=1).mean()) for (eb, c, _), b in zip(frames, fb)}
+            forms[form] = {"value": fv, "ms_per_step": fms / args.steps, "fer": ffer, "gpu_launches": fl}
+        plain = forms["plain_f32"]["value"]
+        forms["flood_f32"] = {"value": value, "vs_plain_f32": value / plain}
+        forms["flood_f16"]["vs_plain_f32"] = forms["flood_f16"]["value"] / plain
+        # int8 layered min-sum on its own workload (rate 5/6, 65536 codewords, 4.0 dB)
+        lw, LB, LZ, lframes = workload_frames(LAYERED_WORKLOAD, rank)
+        lcode = ldpc.Code(LB, LZ)
+        lx = torch.from_numpy(lframes[0][2]).to(dev)        # fp32 LLRs; quantised inside the kernel
+        lp = ldpc.params_for("layered_i8", max_iter=lw.max_iter)
+        lbits = torch.empty((lw.batch, lcode.N), dtype=torch.uint8, device=dev)
+        lit = torch.empty((lw.batch,), dtype=torch.int32, device=dev)
+        for _ in range(args.warmup):
+            ldpc.ldpc_decode_batch(lcode.handle, lp, lx, ldpc.LDPC_LLR_F32, lw.batch, lbits, lit, None, None, 0, stream)
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ldpc.ldpc_profile_reset()
+        ldpc.ldpc_profile_enable(True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ldpc.ldpc_decode_batch(lcode.handle, lp, lx, ldpc.LDPC_LLR_F32, lw.batch, lbits, lit, None, None, 0, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ldpc.ldpc_profile_enable(False)
+        lms = max_over_ranks(e0.elapsed_time(e1))
+        lv = world * args.steps * lw.batch * lcode.K / (lms * 1e-3) / 1e9
+        lit_np = lit.cpu().numpy()
+        forms["layered_i8"] = {"workload": LAYERED_WORKLOAD, "code": lw.code, "value": lv,
+                               "ms_per_decode": lms / args.steps, "avg_iterations": float(lit_np.mean()),
+                               "fer": {f"{lw.ebn0_db[0]:.2f}": float((lbits.cpu().numpy() != lframes[0][1])
+                                                                     .any(axis=1).mean())},
+                               "edge_updates_per_s": float(lcode.E * lit_np.sum() * args.steps / (lms * 1e-3))}
+        line["forms"] = forms
+
+    # ---------------- end to end through the C ABI with host buffers
+    Lh = torch.from_numpy(np.concatenate([L for _, _, L in frames])).pin_memory()
+    ntot = Lh.shape[0]
+    bh = torch.empty((ntot, code.N), dtype=torch.uint8).pin_memory()
+    ih = torch.empty((ntot,), dtype=torch.int32).pin_memory()
+    p32 = params("flood_f32")
+    chunk = 4096
+    for _ in range(max(1, args.warmup)):
+        ldpc.ldpc_decode_host(code.handle, p32, Lh, ntot, bh, ih, args.streams, chunk)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ldpc.ldpc_decode_host(code.handle, p32, Lh, ntot, bh, ih, args.streams, chunk)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    barrier()
+    e2e = {"value": world * args.steps * ntot * code.K / e2e_s / 1e9, "unit": "Gbit/s",
+           "h2d_bytes_per_step": int(Lh.numel() * 4), "d2h_bytes_per_step": int(bh.numel() + ih.numel() * 4),
+           "streams": args.streams, "chunk_codewords": chunk, "api": "ldpc_decode_host"}
+    ok = all(np.array_equal(bh[i * n_per_batch:(i + 1) * n_per_batch].numpy(), bits[i].cpu().numpy())
+             for i in range(len(xs)))
+    e2e["matches_device_path"] = bool(ok)
+    line["e2e"] = e2e
+    ldpc.ldpc_release_host_buffers()
+
+    # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, sample, cores, errs, nfr = oracle_sample_rate(frames, w.code, w.max_iter, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
+                                "sample": sample, "fer_sample": errs / nfr}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -23,14 +23,23 @@ namespace ldpc {
 
 // ------------------------------------------------------------------ phi
 
-// phi(x) = -ln tanh(x/2) for x in [phi(X), X] (and x > 0 in general), from three
-// expansions of the same function, selected without branches:
-//   x < 1/4     : ln(2/x) + x^2/12 - 7 x^4/1440            (Laurent-Taylor series at 0)
-//   1/4 <= x < 5/2 : ln((1 + t)/(1 - t)),  t = e^-x        (closed form)
-//   x >= 5/2    : 2 (t + t^3/3 + t^5/5 + t^7/7)            (2 atanh(t) series, t <= 0.083)
-// built on the hardware approximations ex2/lg2/rcp (PTX *.approx.ftz.f32).  Absolute error
-// below 2e-6 over the range used (checked against the library expm1f/log1pf form and the
-// FP64 oracle by the tests).
+// phi(x) = -ln tanh(x/2) = ln((1 + t)/(1 - t)) with t = e^-x, on the hardware
+// approximations ex2 / lg2 / rcp (PTX *.approx.ftz.f32).  The check rule needs phi twice
+// per edge with different accuracy demands, so there are two evaluations:
+//
+//   psi_in(x)  = phi(x) / ln 2 for the incoming |Q| (base-2 units).  Small values (large x)
+//                are summed and the sum is fed back through phi, so they need RELATIVE
+//                accuracy: for x > 3 the series 2 atanh(t) = 2t + 2t^3/3 + O(t^5) (t < 0.05)
+//                is used; below, the closed form.  As x -> 0 the closed form overflows to
+//                +inf, which the caller clamps to X / ln 2 = psi(phi(X)), the value the
+//                |Q| >= phi(X) clamp of the definition gives.
+//   phi_out(s) = phi(s ln 2) for the exclusive sum s (base-2 units).  The result is added to
+//                the posterior, so ABSOLUTE accuracy suffices for small results; for a small
+//                argument (S = s ln 2 < 1/16) 1 - e^-S loses precision, so it is taken from
+//                its series S (1 - S/2 + S^2/6).  S -> 0 gives +inf, clamped to X by the caller;
+//                large S underflows t to 0 and gives 0.
+// Working in base-2 units removes the ln 2 / log2 e scalings between the two evaluations.
+// Both are checked against the library expm1f/log1pf form and the FP64 oracle by the tests.
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -50,19 +59,23 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-__device__ __forceinline__ float phi_fast(float x)
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+__device__ __forceinline__ float psi_in(float x)
 {
-    const float kLog2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
     const float t = ex2_approx(-x * kLog2e);
-    const bool small = x < 0.25f;
-    const float num = small ? 2.0f : 1.0f + t;
-    const float den = small ? x : 1.0f - t;
-    const float lg = lg2_approx(num * rcp_approx(den)) * kLn2;
-    const float x2 = x * x;
-    const float ab = small ? fmaf(x2, fmaf(x2, -7.0f / 1440.0f, 1.0f / 12.0f), lg) : lg;
-    const float t2 = t * t;
-    const float c = 2.0f * t * fmaf(t2, fmaf(t2, fmaf(t2, 1.0f / 7.0f, 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
-    return x >= 2.5f ? c : ab;
+    const float big = t * fmaf(t * t, (2.0f / 3.0f) * kLog2e, 2.0f * kLog2e);
+    const float mid = lg2_approx((1.0f + t) * rcp_approx(1.0f - t));
+    return x > 3.0f ? big : mid;
+}
+
+__device__ __forceinline__ float phi_out(float s2)
+{
+    const float t = ex2_approx(-s2);
+    const float S = s2 * kLn2;
+    const float den = S < 0.0625f ? S * fmaf(S, fmaf(S, 1.0f / 6.0f, -0.5f), 1.0f) : 1.0f - t;
+    return lg2_approx((1.0f + t) * rcp_approx(den)) * kLn2;
 }
 
 // The plain comparator's phi: the definition log1p(2 / expm1(x)) with the library's
@@ -175,7 +188,7 @@ __global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ ll
     for (int c = w; c < TILE; c += 8) {
         const int64_t cw = (int64_t)tile * TILE + c;
         const int n = n0 + lane;
-        sm[c][lane] = (cw < n_cw && n < N) ? __ldg(llr + cw * N + n) : 0.0f;
+        sm[c][lane] = (cw < n_cw && n < N) ? __ldg(llr + cw * N + n) + 0.0f : 0.0f;  // -0 -> +0
     }
     __syncthreads();
     for (int nn = w; nn < 32; nn += 8) {
@@ -238,16 +251,25 @@ __global__ void __launch_bounds__(256) k_deinterleave(const float *__restrict__ 
 // One warp per (tile, check m, lane group).  For every edge k of check m:
 //   Q_k = APP_n - R_k (R = 0 in the first iteration, FIRST), a_k = phi(clamp |Q_k|),
 //   R'_k = sgn_k * min(X, phi(sum_{k' != k} a_k')),  sgn_k = product of the other signs.
-// The exclusive sums are S - a_k for every edge but the largest a (where S - a_k would
-// cancel); the largest edge's sum is formed directly.  Also the syndrome bit of the
-// previous hard decisions (APP < 0) when check_syn.
+// a_k carries the sign of Q_k in its sign bit.  The exclusive sums are S - a_k, except
+// for an edge holding more than half of S, where the subtraction would cancel: its sum
+// is formed directly.  When check_syn, the parity of the previous hard decisions over the
+// check (the XOR of the APP sign bits; APP never holds -0) marks unsatisfied codewords.
+#ifndef LDPC_CN_MINB
+#define LDPC_CN_MINB 4  // resident 256-thread blocks per SM the check-node kernel is compiled for
+#endif
+#ifndef LDPC_CN_V8
+#define LDPC_CN_V8 4    // codewords per lane for codes with check degree <= 8
+#endif
+
 template <int DMAX, int V, typename MsgT, bool FIRST>
-__global__ void __launch_bounds__(256) k_flood_cn(const CodeDev *__restrict__ cd, const float *__restrict__ app,
-                                                  MsgT *__restrict__ R, const int32_t *__restrict__ done_at,
-                                                  int32_t *__restrict__ unsat, int t, int check_syn,
-                                                  int64_t total_warps, float X, float phiX)
+__global__ void __launch_bounds__(256, LDPC_CN_MINB) k_flood_cn(const CodeDev *__restrict__ cd, const float *__restrict__ app,
+                                                     MsgT *__restrict__ R, const int32_t *__restrict__ done_at,
+                                                     int32_t *__restrict__ unsat, int t, int check_syn,
+                                                     int64_t total_warps, float X)
 {
     constexpr int WPN = TILE / (32 * V);
+    constexpr uint32_t kSign = 0x80000000u;
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gw >= total_warps) return;
     const int lane = threadIdx.x & 31;
@@ -271,11 +293,17 @@ __global__ void __launch_bounds__(256) k_flood_cn(const CodeDev *__restrict__ cd
     const int dc = cd->rowptr[l + 1] - b0;
     const float *ap = app + (int64_t)tile * cd->N * TILE + slot;
     MsgT *rp = R + (int64_t)tile * cd->E * TILE + slot;
+    const float Xb = X * kLog2e;  // psi(phi(X)) = X / ln 2
 
     float a[DMAX][V];
-    uint32_t neg[V], par[V];
+    uint32_t par[V], sg[V];
+    float S[V], amax[V];
 #pragma unroll
-    for (int v = 0; v < V; v++) neg[v] = par[v] = 0u;
+    for (int v = 0; v < V; v++) {
+        par[v] = sg[v] = 0u;
+        S[v] = 0.0f;
+        amax[v] = 0.0f;
+    }
 
 #pragma unroll
     for (int k = 0; k < DMAX; k++) {
@@ -298,38 +326,32 @@ __global__ void __launch_bounds__(256) k_flood_cn(const CodeDev *__restrict__ cd
             }
 #pragma unroll
             for (int v = 0; v < V; v++) {
-                par[v] ^= av[v] < 0.0f ? 1u : 0u;
-                neg[v] |= (q[v] < 0.0f ? 1u : 0u) << k;
-                a[k][v] = phi_fast(fminf(fmaxf(fabsf(q[v]), phiX), X));
+                par[v] ^= __float_as_uint(av[v]);
+                const float mag = fminf(psi_in(fminf(fabsf(q[v]), X)), Xb);
+                S[v] += mag;
+                amax[v] = fmaxf(amax[v], mag);
+                const uint32_t qs = __float_as_uint(q[v]) & kSign;
+                sg[v] ^= qs;
+                a[k][v] = __uint_as_float(__float_as_uint(mag) | qs);
             }
         }
     }
 
 #pragma unroll
     for (int v = 0; v < V; v++) {
-        float S = 0.0f, amax = -1.0f;
-        int kmax = 0;
-#pragma unroll
-        for (int k = 0; k < DMAX; k++) {
-            if (k < dc) {
-                S += a[k][v];
-                if (a[k][v] > amax) {
-                    amax = a[k][v];
-                    kmax = k;
-                }
-            }
-        }
+        // direct sum of the others for a dominant edge (a > S/2 can hold for one edge only)
         float Sx = 0.0f;
 #pragma unroll
         for (int k = 0; k < DMAX; k++)
-            if (k < dc && k != kmax) Sx += a[k][v];
-        const uint32_t P = __popc(neg[v]) & 1u;
+            if (k < dc) Sx += (fabsf(a[k][v]) == amax[v]) ? 0.0f : fabsf(a[k][v]);
+        const float sx = (amax[v] > 0.5f * S[v]) ? Sx : S[v] - amax[v];
 #pragma unroll
         for (int k = 0; k < DMAX; k++) {
             if (k < dc) {
-                const float ex = (k == kmax) ? Sx : S - a[k][v];
-                const float mag = fminf(phi_fast(ex), X);
-                a[k][v] = (P ^ ((neg[v] >> k) & 1u)) ? -mag : mag;
+                const float ak = fabsf(a[k][v]);
+                const float ex = (ak == amax[v]) ? sx : S[v] - ak;
+                const float mag = fminf(phi_out(ex), X);
+                a[k][v] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(a[k][v]) ^ sg[v]) & kSign));
             }
         }
     }
@@ -346,7 +368,7 @@ __global__ void __launch_bounds__(256) k_flood_cn(const CodeDev *__restrict__ cd
     if (check_syn) {
 #pragma unroll
         for (int v = 0; v < V; v++)
-            if (par[v] && dn[v] == 0) unsat[cw + v] = t;
+            if ((par[v] & kSign) && dn[v] == 0) unsat[cw + v] = t;
     }
 }
 
@@ -404,6 +426,8 @@ __global__ void __launch_bounds__(256) k_flood_vn(const CodeDev *__restrict__ cd
 #pragma unroll
         for (int v = 0; v < V; v++) s[v] += rv[v];
     }
+#pragma unroll
+    for (int v = 0; v < V; v++) s[v] += 0.0f;  // -0 -> +0: the APP sign bit is the hard decision
     float *dst = app + ((int64_t)tile * N + n) * TILE + slot;
     if (all) {
         Msg<float, V>::store(dst, s);
@@ -528,7 +552,6 @@ static cudaError_t flood_iterations(const CodeDev &h, const CodeDev *d, const ld
 {
     constexpr int WPN = TILE / (32 * V);
     const float X = p.phi_clamp;
-    const float phiX = (float)log1p(2.0 / expm1((double)X));
     const int64_t cn_warps = ntiles * h.M * WPN, vn_warps = ntiles * h.N * WPN;
     const unsigned cn_blocks = (unsigned)((cn_warps + 7) / 8), vn_blocks = (unsigned)((vn_warps + 7) / 8);
     MsgT *R = reinterpret_cast<MsgT *>(ws.R);
@@ -537,10 +560,10 @@ static cudaError_t flood_iterations(const CodeDev &h, const CodeDev *d, const ld
             LaunchScope ls(F_CN, s);
             if (t == 1)
                 k_flood_cn<DMAX, V, MsgT, true><<<cn_blocks, 256, 0, s>>>(d, ws.L, R, ws.done_at, ws.unsat, t, 0,
-                                                                         cn_warps, X, phiX);
+                                                                         cn_warps, X);
             else
                 k_flood_cn<DMAX, V, MsgT, false><<<cn_blocks, 256, 0, s>>>(d, ws.app, R, ws.done_at, ws.unsat, t,
-                                                                          p.early_exit, cn_warps, X, phiX);
+                                                                          p.early_exit, cn_warps, X);
         }
         {
             LaunchScope ls(F_VN, s);
@@ -594,8 +617,8 @@ cudaError_t flood_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_p
         else if (h.dc_max <= 16) e = plain_iterations<16>(h, d, p, ws, ntiles, s);
         else e = plain_iterations<32>(h, d, p, ws, ntiles, s);
     } else if (h.dc_max <= 8) {
-        e = f16 ? flood_iterations<8, 4, __half>(h, d, p, ws, ntiles, s)
-                : flood_iterations<8, 4, float>(h, d, p, ws, ntiles, s);
+        e = f16 ? flood_iterations<8, LDPC_CN_V8, __half>(h, d, p, ws, ntiles, s)
+                : flood_iterations<8, LDPC_CN_V8, float>(h, d, p, ws, ntiles, s);
     } else if (h.dc_max <= 16) {
         e = f16 ? flood_iterations<16, 2, __half>(h, d, p, ws, ntiles, s)
                 : flood_iterations<16, 2, float>(h, d, p, ws, ntiles, s);
