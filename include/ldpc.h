@@ -147,6 +147,35 @@ ldpc_status ldpc_profile_reset(void);
 int64_t ldpc_launch_count(void);
 void ldpc_launch_count_reset(void);
 
+/* Flooding decode that allocates no device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory at decode time - for example a real-time receive pipeline that reserves all
+ * of its memory at start-up (a cudaMalloc can synchronize the device and has no latency
+ * bound), or a host process whose device memory is owned by another framework's pool.
+ * It runs the same flooding sum-product kernels as ldpc_decode_batch, but their scratch
+ * (interleaved LLRs, posteriors, messages and per-codeword flags) lives in one fixed
+ * array of LDPC_STATIC_SCRATCH_BYTES bytes compiled into the library.  Every GPU that
+ * loads the library holds that array until the process exits.
+ *   - Same arguments and layouts as ldpc_decode_batch with llr_type LDPC_LLR_F32 and no
+ *     workspace; only the flooding SPA forms (F32 / F16 messages) are accepted.
+ *   - n_cw must satisfy ldpc_workspace_size(code, p, n_cw) <= LDPC_STATIC_SCRATCH_BYTES;
+ *     larger batches are rejected with LDPC_ENOMEM before anything is launched (decode
+ *     them in several calls).  For the N = 1944 rate-1/2 code with FP32 messages this is
+ *     up to 896 codewords per call (the scratch grows in tiles of 128 codewords).
+ *   - The first call on each device looks up the array's device address (with that device
+ *     current) and keeps it; make that first call before any stream capture begins.
+ *   - All calls share the one array and it keeps whatever the last call left in it (the
+ *     kernels initialise every part they read).  Calls whose work overlaps on the GPU -
+ *     on different streams, or from different host threads without ordering - corrupt each
+ *     other's scratch: issue them on one stream, or order them.
+ * Returns LDPC_OK, LDPC_EINVAL / LDPC_ENOTSUP for bad arguments, LDPC_ENOMEM for a batch
+ * beyond the array, LDPC_ECUDA for a failed address lookup or launch. */
+#define LDPC_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+ldpc_status ldpc_decode_batch_static(const ldpc_code *code, const ldpc_decode_params *p, const float *llr_dev,
+                                     int64_t n_cw, uint8_t *bits_dev, int32_t *iters_dev, float *app_dev,
+                                     void *stream);
+
 /* Message for the calling thread's most recent failure ("" if none).  Valid until the
  * thread's next call into the library. */
 const char *ldpc_last_error(void);

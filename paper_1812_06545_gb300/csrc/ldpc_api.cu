@@ -79,6 +79,8 @@ void drain_pending()
 
 namespace ldpc {
 
+void set_error(const char *msg) { g_err = msg; }
+
 LaunchScope::LaunchScope(int fam, cudaStream_t s) : family(fam), stream(s), on(false)
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -61,6 +61,9 @@ cudaError_t layered_decode(const CodeDev &host, const CodeDev *dev, const ldpc_d
                            cudaStream_t s);
 int layered_supported(const CodeDev &host);
 
+// Record a message for ldpc_last_error() on the calling thread.
+void set_error(const char *msg);
+
 }  // namespace ldpc
 
 struct ldpc_code {

@@ -59,6 +59,7 @@ def lib():
             "ldpc_workspace_size": [vp, vp, i64, vp],
             "ldpc_decode_batch": [vp, vp, vp, i32, i64, vp, vp, vp, vp, sz, vp],
             "ldpc_decode_host": [vp, vp, vp, i64, vp, vp, i32, i64],
+            "ldpc_decode_batch_static": [vp, vp, vp, i64, vp, vp, vp, vp],
             "ldpc_profile_enable": [i32],
             "ldpc_profile_read": [i32, vp, vp],
             "ldpc_profile_reset": [],
@@ -145,6 +146,21 @@ def ldpc_decode_batch(handle: int, params: DecodeParams, llr, llr_type: int, n_c
     _check(lib().ldpc_decode_batch(handle, C.byref(params), _ptr(llr), int(llr_type), int(n_cw), _ptr(bits),
                                    _ptr(iters), _ptr(app), _ptr(workspace), int(workspace_bytes), _stream(stream)),
            "ldpc_decode_batch")
+
+
+LDPC_STATIC_SCRATCH_BYTES = 32 << 20
+
+
+def ldpc_decode_batch_static(handle: int, params: DecodeParams, llr, n_cw: int, bits, iters, app=None,
+                             stream=None) -> None:
+    """Flooding decode whose scratch is the library's fixed device array (no allocation).
+
+    For callers that must not allocate device memory while decoding; batches needing more
+    than LDPC_STATIC_SCRATCH_BYTES of scratch are rejected, and calls that overlap on the
+    GPU share (and corrupt) the one array.  The first call on a device looks up the array's
+    address, so make it before any stream capture."""
+    _check(lib().ldpc_decode_batch_static(handle, C.byref(params), _ptr(llr), int(n_cw), _ptr(bits), _ptr(iters),
+                                          _ptr(app), _stream(stream)), "ldpc_decode_batch_static")
 
 
 def ldpc_decode_host(handle: int, params: DecodeParams, llr_host, n_cw: int, bits_host, iters_host=None,
