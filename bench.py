@@ -35,6 +35,37 @@ METRIC = "decoded info Gbit/s and p99 latency at equal FER vs plain FP32 floodin
 WORKLOAD = "flood_n1944_b8192_sweep"
 LAYERED_WORKLOAD = "layered_i8_n1944_r56_b65536"
 CN_SOURCE = os.path.join(ROOT, "paper_1812_06545_gb300", "csrc", "flood_kernels.cu")
+SLOTS_SOURCE = os.path.join(ROOT, "paper_1812_06545_gb300", "csrc", "flood_slots.cu")
+
+
+def streaming_roofline(ldpc, iters_np, steps, N, E, T, hbm_peak, peak_src):
+    """HBM roofline of the streaming check-node kernel from the library's event timing and
+    the iteration counts (CN(t) runs while t <= iters + 1, VN(t) while t <= iters)."""
+    n_cn, cn_ms = ldpc.ldpc_profile_read("check_node")
+    n_vn, vn_ms = ldpc.ldpc_profile_read("variable_node")
+    cn_bytes = vn_bytes = 0
+    for it in iters_np:
+        last_cn = np.where(it < T, it + 1, T)
+        for t in range(1, T + 1):
+            cn_bytes += int((last_cn >= t).sum()) * (4 * N + 4 * E + (4 * E if t >= 2 else 0))
+            vn_bytes += int((it >= t).sum()) * (4 * E + 8 * N)
+    cn_gbs = steps * cn_bytes / (cn_ms * 1e-3) / 1e9 if cn_ms > 0 else None
+    vn_gbs = steps * vn_bytes / (vn_ms * 1e-3) / 1e9 if vn_ms > 0 else None
+    traffic = None
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
+        ent = tr.get("k_flood_cn")
+        if ent and ent.get("source_sha256") == hashlib.sha256(open(CN_SOURCE, "rb").read()).hexdigest():
+            traffic = ent.get("bytes_per_launch_full_size")
+    except Exception:
+        pass
+    return {"bound": "hbm", "kernel": "k_flood_cn (check-node phase)", "achieved": cn_gbs, "peak": hbm_peak,
+            "unit": "GB/s", "frac": (cn_gbs / hbm_peak) if cn_gbs else None, "peak_source": peak_src,
+            "traffic": traffic, "launches": n_cn, "avg_launch_ms": cn_ms / max(n_cn, 1),
+            "algorithmic_bytes_per_cw_iteration": 4 * N + 8 * E,
+            "variable_node": {"achieved": vn_gbs, "frac": (vn_gbs / hbm_peak) if vn_gbs else None,
+                              "launches": n_vn, "avg_launch_ms": vn_ms / max(n_vn, 1),
+                              "algorithmic_bytes_per_cw_iteration": 4 * E + 8 * N}}
 
 
 def parse_args():
@@ -302,20 +333,6 @@ def main():
         fer[f"{eb:.2f}"] = float((bn != c).any(axis=1).mean())
         iters_np.append(it.cpu().numpy())
 
-    # roofline of the check-node kernel: algorithmic bytes of every launch in the timed region
-    n_cn, cn_ms = ldpc.ldpc_profile_read("check_node")
-    n_vn, vn_ms = ldpc.ldpc_profile_read("variable_node")
-    N, E, T = code.N, code.E, w.max_iter
-    cn_bytes = vn_bytes = 0
-    for it in iters_np:
-        last_cn = np.where(it < T, it + 1, T)        # CN(t) runs for t <= iters + 1 (syndrome check)
-        for t in range(1, T + 1):
-            a_cn = int((last_cn >= t).sum())
-            a_vn = int((it >= t).sum())
-            cn_bytes += a_cn * (4 * N + 4 * E + (4 * E if t >= 2 else 0))
-            vn_bytes += a_vn * (4 * E + 8 * N)
-    cn_bytes *= args.steps
-    vn_bytes *= args.steps
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -323,32 +340,39 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    cn_gbs = cn_bytes / (cn_ms * 1e-3) / 1e9 if cn_ms > 0 else None
-    vn_gbs = vn_bytes / (vn_ms * 1e-3) / 1e9 if vn_ms > 0 else None
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    N, E, T = code.N, code.E, w.max_iter
+
+    # roofline of the slot decoder (the headline form's only kernel): compute-bound; every
+    # edge update needs two phi evaluations, i.e. at least two exponentials and two
+    # logarithms on the special-function units (16 per clock per SM)
+    n_sl, sl_ms = ldpc.ldpc_profile_read("slots")
+    edge_updates = args.steps * E * int(sum(int(it.sum()) for it in iters_np))
+    sfu_peak = n_sm * 16 * sm_mhz * 1e6 / 4 / 1e9                     # Gedge/s
+    achieved = edge_updates / (sl_ms * 1e-3) / 1e9 if sl_ms > 0 else None
     traffic = None
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
-        src_hash = hashlib.sha256(open(CN_SOURCE, "rb").read()).hexdigest()
-        ent = tr.get("k_flood_cn")
-        if ent and ent.get("source_sha256") == src_hash:
+        ent = tr.get("k_flood_slots")
+        if ent and ent.get("source_sha256") == hashlib.sha256(open(SLOTS_SOURCE, "rb").read()).hexdigest():
             traffic = ent.get("bytes_per_launch_full_size")
     except Exception:
         pass
-    roofline = {"bound": "hbm", "kernel": "k_flood_cn (check-node phase)", "achieved": cn_gbs, "peak": hbm_peak,
-                "unit": "GB/s", "frac": (cn_gbs / hbm_peak) if cn_gbs else None, "peak_source": peak_src,
-                "traffic": traffic, "launches": n_cn, "avg_launch_ms": cn_ms / max(n_cn, 1),
-                "algorithmic_bytes_per_cw_iteration": 4 * N + 8 * E,
-                "variable_node": {"achieved": vn_gbs, "frac": (vn_gbs / hbm_peak) if vn_gbs else None,
-                                  "launches": n_vn, "avg_launch_ms": vn_ms / max(n_vn, 1),
-                                  "algorithmic_bytes_per_cw_iteration": 4 * E + 8 * N}}
+    roofline = {"bound": "alu", "kernel": "k_flood_slots (on-chip flooding slot decoder)", "achieved": achieved,
+                "peak": sfu_peak, "unit": "Gedge/s", "frac": (achieved / sfu_peak) if achieved else None,
+                "peak_source": f"derived: {n_sm} SMs x 16 SFU ops/clk x {sm_mhz:.0f} MHz / 4 SFU ops per edge update",
+                "traffic": traffic, "launches": n_sl, "avg_launch_ms": sl_ms / max(n_sl, 1),
+                "algorithmic_work": "edge updates = E x iterations run, summed over codewords"}
 
     line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": "flooding sum-product, FP32 messages", "code": w.code,
+            "config": {"workload": WORKLOAD, "form": "flooding sum-product, FP32 messages (on-chip slot decoder)",
+                       "code": w.code,
                        "N": code.N, "K": code.K, "batch": n_per_batch, "ebn0_db": w.ebn0_db,
                        "max_iter": w.max_iter, "early_exit": True, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (7 x 63.7 MB LLR batches + 178 MB messages per batch)"},
+                       "l2": "inputs larger than L2 (7 x 63.7 MB LLR batches per step)"},
             "latency_ms": {"what": "one 8192-codeword decode call", "p50": float(np.percentile(lat, 50)),
                            "p99": float(np.percentile(lat, 99))},
             "avg_iterations": float(np.mean(np.concatenate(iters_np))), "fer": fer,
@@ -357,15 +381,20 @@ def main():
     # ---------------- other forms on the same inputs
     if not args.no_forms:
         forms = {}
-        for form in ("flood_f16", "plain_f32"):
-            fms, fl, fb, fi = run_form(form, args.steps, args.warmup)
+        for form in ("flood_f16", "stream_f32", "stream_f16", "plain_f32"):
+            prof = form.startswith("stream")
+            fms, fl, fb, fi = run_form(form, args.steps, args.warmup, profile=prof)
             fms = max_over_ranks(fms)
             fv = units * code.K / (fms * 1e-3) / 1e9
             ffer = {f"{eb:.2f}": float((b.cpu().numpy() != c).any(axis=1).mean()) for (eb, c, _), b in zip(frames, fb)}
             forms[form] = {"value": fv, "ms_per_step": fms / args.steps, "fer": ffer, "gpu_launches": fl}
+            if prof:
+                forms[form]["roofline"] = streaming_roofline(ldpc, [x.cpu().numpy() for x in fi], args.steps, N, E, T,
+                                                             hbm_peak, peak_src)
         plain = forms["plain_f32"]["value"]
         forms["flood_f32"] = {"value": value, "vs_plain_f32": value / plain}
-        forms["flood_f16"]["vs_plain_f32"] = forms["flood_f16"]["value"] / plain
+        for f in ("flood_f16", "stream_f32", "stream_f16"):
+            forms[f]["vs_plain_f32"] = forms[f]["value"] / plain
         # int8 layered min-sum on its own workload (rate 5/6, 65536 codewords, 4.0 dB)
         lw, LB, LZ, lframes = workload_frames(LAYERED_WORKLOAD, rank)
         lcode = ldpc.Code(LB, LZ)

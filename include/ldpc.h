@@ -48,9 +48,14 @@ typedef enum { LDPC_ALGO_SPA = 0, LDPC_ALGO_NMS = 1 } ldpc_algo;
 typedef enum { LDPC_MSG_F32 = 0, LDPC_MSG_F16 = 1, LDPC_MSG_I8 = 2 } ldpc_msg_type;
 typedef enum { LDPC_LLR_F32 = 0, LDPC_LLR_I8 = 1 } ldpc_llr_type;
 typedef enum {
-    LDPC_IMPL_AUTO = 0,  /* the optimised kernels for the requested form                */
-    LDPC_IMPL_PLAIN = 1  /* the plain FP32 flooding comparator (one codeword per thread, */
-                         /* library expm1f/log1pf phi, no early-exit skipping)           */
+    LDPC_IMPL_AUTO = 0,     /* the fastest kernels for the requested form: for flooding, the */
+                            /* on-chip slot decoder when one codeword's posterior and        */
+                            /* messages fit in shared memory, else the streaming kernels     */
+    LDPC_IMPL_PLAIN = 1,    /* the plain FP32 flooding comparator (one codeword per thread,  */
+                            /* library expm1f/log1pf phi, state streamed through HBM)        */
+    LDPC_IMPL_STREAMING = 2 /* flooding with all state streamed through HBM in the          */
+                            /* codeword-interleaved layout (check-node and variable-node    */
+                            /* kernels per iteration)                                        */
 } ldpc_impl;
 
 /* Opaque code object (library-owned, immutable after creation, usable from any thread). */
@@ -138,7 +143,7 @@ void ldpc_release_host_buffers(void);
  * events on its launch stream; ldpc_profile_read returns, per kernel family, the number
  * of launches and the summed event time in milliseconds (it synchronizes the pending
  * events).  Families: 0 interleave, 1 check-node, 2 variable-node, 3 deinterleave,
- * 4 layered, 5 plain check-node, 6 plain variable-node. */
+ * 4 layered, 5 plain check-node, 6 plain variable-node, 7 on-chip flooding slot decoder. */
 ldpc_status ldpc_profile_enable(int32_t on);
 ldpc_status ldpc_profile_read(int32_t family, int64_t *launches, double *ms);
 ldpc_status ldpc_profile_reset(void);
@@ -161,8 +166,10 @@ void ldpc_launch_count_reset(void);
  *     workspace; only the flooding SPA forms (F32 / F16 messages) are accepted.
  *   - n_cw must satisfy ldpc_workspace_size(code, p, n_cw) <= LDPC_STATIC_SCRATCH_BYTES;
  *     larger batches are rejected with LDPC_ENOMEM before anything is launched (decode
- *     them in several calls).  For the N = 1944 rate-1/2 code with FP32 messages this is
- *     up to 896 codewords per call (the scratch grows in tiles of 128 codewords).
+ *     them in several calls).  With LDPC_IMPL_AUTO a code whose codeword state fits on
+ *     chip needs only a few bytes of scratch, so any batch fits; with LDPC_IMPL_STREAMING
+ *     or LDPC_IMPL_PLAIN the scratch grows in tiles of 128 codewords (up to 896 codewords
+ *     of the N = 1944 rate-1/2 code with FP32 messages).
  *   - The first call on each device looks up the array's device address (with that device
  *     current) and keeps it; make that first call before any stream capture begins.
  *   - All calls share the one array and it keeps whatever the last call left in it (the

@@ -220,7 +220,8 @@ static ldpc_status check_params(const ldpc_code *c, const ldpc_decode_params *p,
     if (p->early_exit != 0 && p->early_exit != 1) return fail(LDPC_EINVAL, "early_exit must be 0 or 1");
     for (int i = 0; i < 4; i++)
         if (p->reserved[i] != 0) return fail(LDPC_EINVAL, "reserved fields must be zero");
-    if (p->impl != LDPC_IMPL_AUTO && p->impl != LDPC_IMPL_PLAIN) return fail(LDPC_EINVAL, "bad impl");
+    if (p->impl != LDPC_IMPL_AUTO && p->impl != LDPC_IMPL_PLAIN && p->impl != LDPC_IMPL_STREAMING)
+        return fail(LDPC_EINVAL, "bad impl");
     if (p->sched == LDPC_SCHED_FLOODING && p->algo == LDPC_ALGO_SPA) {
         if (p->msg != LDPC_MSG_F32 && p->msg != LDPC_MSG_F16)
             return fail(LDPC_ENOTSUP, "flooding SPA stores messages as F32 or F16");
@@ -251,9 +252,17 @@ static ldpc_status check_params(const ldpc_code *c, const ldpc_decode_params *p,
     return fail(LDPC_ENOTSUP, "unsupported sched/algo combination (%d, %d)", p->sched, p->algo);
 }
 
+// The on-chip slot decoder serves the flooding forms whenever one codeword's state fits in
+// a CTA's shared memory; LDPC_IMPL_STREAMING and the plain comparator use the HBM layout.
+static bool use_slots(const ldpc_code *c, const ldpc_decode_params *p)
+{
+    return p->sched == LDPC_SCHED_FLOODING && p->impl == LDPC_IMPL_AUTO && ldpc::slots_supported(c->host, p->msg);
+}
+
 static size_t ws_bytes(const ldpc_code *c, const ldpc_decode_params *p, int64_t n_cw)
 {
     if (p->sched == LDPC_SCHED_LAYERED || n_cw == 0) return 0;
+    if (use_slots(c, p)) return ldpc::SLOTS_WS_BYTES;
     return ldpc::flood_ws_layout(c->host, n_cw, p->msg, nullptr, nullptr);
 }
 
@@ -297,9 +306,13 @@ ldpc_status ldpc_decode_batch(const ldpc_code *c, const ldpc_decode_params *p, c
         }
         own = true;
     }
-    ldpc::FloodWs w;
-    ldpc::flood_ws_layout(c->host, n_cw, p->msg, &w, static_cast<char *>(ws));
-    e = ldpc::flood_decode(c->host, c->dev, *p, static_cast<const float *>(llr), n_cw, bits, iters, app, w, s);
+    if (use_slots(c, p)) {
+        e = ldpc::slots_decode(c->host, c->dev, *p, static_cast<const float *>(llr), n_cw, bits, iters, app, ws, s);
+    } else {
+        ldpc::FloodWs w;
+        ldpc::flood_ws_layout(c->host, n_cw, p->msg, &w, static_cast<char *>(ws));
+        e = ldpc::flood_decode(c->host, c->dev, *p, static_cast<const float *>(llr), n_cw, bits, iters, app, w, s);
+    }
     if (own) {
         cudaError_t e2 = cudaFreeAsync(ws, s);
         if (e == cudaSuccess) e = e2;

@@ -33,7 +33,7 @@ struct CodeDev {
 
 // Per-kernel-family timing and launch accounting (see ldpc_profile_* in ldpc.h).
 enum Family { F_INTERLEAVE = 0, F_CN = 1, F_VN = 2, F_DEINTERLEAVE = 3, F_LAYERED = 4, F_PLAIN_CN = 5,
-              F_PLAIN_VN = 6, F_COUNT = 7 };
+              F_PLAIN_VN = 6, F_SLOTS = 7, F_COUNT = 8 };
 struct LaunchScope {
     LaunchScope(int family, cudaStream_t s);
     ~LaunchScope();
@@ -60,6 +60,13 @@ cudaError_t layered_decode(const CodeDev &host, const CodeDev *dev, const ldpc_d
                            int llr_type, int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out,
                            cudaStream_t s);
 int layered_supported(const CodeDev &host);
+
+// On-chip slot decoder for the flooding forms (flood_slots.cu).  counter: 8 bytes of
+// device memory, zeroed on the stream before the launch.
+constexpr size_t SLOTS_WS_BYTES = 256;
+int slots_supported(const CodeDev &host, int msg);
+cudaError_t slots_decode(const CodeDev &host, const CodeDev *dev, const ldpc_decode_params &p, const float *llr,
+                         int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out, void *counter, cudaStream_t s);
 
 // Record a message for ldpc_last_error() on the calling thread.
 void set_error(const char *msg);

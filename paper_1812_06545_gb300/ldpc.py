@@ -22,9 +22,9 @@ LDPC_SCHED_FLOODING, LDPC_SCHED_LAYERED = 0, 1
 LDPC_ALGO_SPA, LDPC_ALGO_NMS = 0, 1
 LDPC_MSG_F32, LDPC_MSG_F16, LDPC_MSG_I8 = 0, 1, 2
 LDPC_LLR_F32, LDPC_LLR_I8 = 0, 1
-LDPC_IMPL_AUTO, LDPC_IMPL_PLAIN = 0, 1
+LDPC_IMPL_AUTO, LDPC_IMPL_PLAIN, LDPC_IMPL_STREAMING = 0, 1, 2
 FAMILIES = {"interleave": 0, "check_node": 1, "variable_node": 2, "deinterleave": 3, "layered": 4,
-            "plain_check_node": 5, "plain_variable_node": 6}
+            "plain_check_node": 5, "plain_variable_node": 6, "slots": 7}
 
 
 class LdpcError(RuntimeError):
@@ -223,6 +223,8 @@ FORMS = {
     "flood_f32": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F32),
     "flood_f16": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F16),
     "plain_f32": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F32, impl=LDPC_IMPL_PLAIN),
+    "stream_f32": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F32, impl=LDPC_IMPL_STREAMING),
+    "stream_f16": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F16, impl=LDPC_IMPL_STREAMING),
     "layered_i8": dict(sched=LDPC_SCHED_LAYERED, algo=LDPC_ALGO_NMS, msg=LDPC_MSG_I8),
 }
 

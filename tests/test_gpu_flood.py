@@ -34,7 +34,7 @@ def run(name, form, L, dev, **kw):
     return app.cpu().numpy(), bits.cpu().numpy(), iters.cpu().numpy()
 
 
-@pytest.mark.parametrize("form", ["flood_f32", "plain_f32"])
+@pytest.mark.parametrize("form", ["flood_f32", "stream_f32", "plain_f32"])
 @pytest.mark.parametrize("name,n,eb", CASES)
 def test_fp32_posterior_first_three_iterations(cuda_dev, form, name, n, eb):
     _, _, c, L = I.make_frames(name, n, eb, 3, 4)
@@ -48,8 +48,9 @@ def test_fp32_posterior_first_three_iterations(cuda_dev, form, name, n, eb):
         assert np.array_equal(bits, (app < 0).astype(np.uint8))
 
 
+@pytest.mark.parametrize("form", ["flood_f16", "stream_f16"])
 @pytest.mark.parametrize("name,n,eb", CASES)
-def test_fp16_messages_first_three_iterations(cuda_dev, name, n, eb):
+def test_fp16_messages_first_three_iterations(cuda_dev, form, name, n, eb):
     # The oracle models half-precision message storage (messages rounded to binary16).
     # Beyond the fp32 tolerance the two may differ by the rounding of each incoming
     # message (FP32 vs FP64 values on either side of a binary16 rounding boundary), carried
@@ -57,14 +58,14 @@ def test_fp16_messages_first_three_iterations(cuda_dev, name, n, eb):
     _, _, c, L = I.make_frames(name, n, eb, 5, 6)
     oc = oracle_code(name)
     for T in (1, 2, 3):
-        app, _, _ = run(name, "flood_f16", L, cuda_dev, max_iter=T, early_exit=0)
+        app, _, _ = run(name, form, L, cuda_dev, max_iter=T, early_exit=0)
         ref, _, _, R = oc.spa_flood(L, T, early_exit=False, fp16_msgs=True, return_messages=True)
         tol = FP32_TOL * np.maximum(1.0, np.abs(ref)) + 4 * 2.0 ** -11 * oc.incoming_message_sum(R)
         d = np.abs(app - ref)
         assert (d <= tol).all(), (name, T, (d - tol).max())
 
 
-@pytest.mark.parametrize("form", ["flood_f32", "flood_f16", "plain_f32"])
+@pytest.mark.parametrize("form", ["flood_f32", "flood_f16", "stream_f32", "stream_f16", "plain_f32"])
 def test_early_exit_and_fer_full_size(cuda_dev, form):
     # 8192 codewords of the rate-1/2 N=1944 code, early exit, max 20 iterations, at 1.5
     # and 2.0 dB, in the launch configuration the benchmark times: the GPU frame error rate
@@ -74,7 +75,7 @@ def test_early_exit_and_fer_full_size(cuda_dev, form):
     # converges, 20 iterations of the non-converging dynamics amplify the binary16 rounding).
     name = "qc12x24_z81_s2"
     oc = oracle_code(name)
-    f16 = form == "flood_f16"
+    f16 = form.endswith("f16")
     mism = tot = 0
     for eb, seed in ((1.5, 23), (2.0, 25)):
         _, _, c, L = I.make_frames(name, 8192, eb, 20, seed)
@@ -96,12 +97,15 @@ def test_early_exit_and_fer_full_size(cuda_dev, form):
         assert mism <= 1e-4 * tot, (form, mism, tot)
 
 
-def test_batch_invariance(cuda_dev):
+@pytest.mark.parametrize("form", ["flood_f32", "flood_f16", "stream_f32"])
+def test_batch_invariance(cuda_dev, form):
+    # a codeword decodes to the same bits, posterior and iteration count alone and in a
+    # batch (whatever slot or tile position it lands in)
     name = "qc12x24_z81_s2"
-    _, _, c, L = I.make_frames(name, 300, 1.75, 7, 8)
-    app_all, _, it_all = run(name, "flood_f32", L, cuda_dev, max_iter=20, early_exit=1)
-    for i in (0, 127, 128, 299):
-        app1, _, it1 = run(name, "flood_f32", L[i:i + 1].copy(), cuda_dev, max_iter=20, early_exit=1)
+    _, _, c, L = I.make_frames(name, 3000, 1.75, 7, 8)
+    app_all, _, it_all = run(name, form, L, cuda_dev, max_iter=20, early_exit=1)
+    for i in (0, 127, 128, 1499, 2999):
+        app1, _, it1 = run(name, form, L[i:i + 1].copy(), cuda_dev, max_iter=20, early_exit=1)
         assert np.array_equal(app1[0], app_all[i]) and it1[0] == it_all[i]
 
 
@@ -118,6 +122,18 @@ def test_small_and_empty_batches(cuda_dev):
     assert rel_err(app, ref).max() <= FP32_TOL and np.array_equal(iters, riters)
 
 
+def test_slot_and_streaming_paths_agree(cuda_dev):
+    # the on-chip slot decoder and the HBM-streaming kernels compute the same iteration;
+    # they differ only in summation order, so decisions and iteration counts agree
+    name = "qc12x24_z81_s2"
+    _, _, c, L = I.make_frames(name, 4096, 2.0, 13, 14)
+    a1, b1, i1 = run(name, "flood_f32", L, cuda_dev, max_iter=20, early_exit=1)
+    a2, b2, i2 = run(name, "stream_f32", L, cuda_dev, max_iter=20, early_exit=1)
+    conv = (i1 < 20) & (i2 < 20)
+    assert np.array_equal(b1[conv], b2[conv]) and np.array_equal(i1[conv], i2[conv])
+    assert (b1 == b2).all(axis=1).mean() >= 0.999
+
+
 def test_eq1_code_z1_and_extreme_shifts(cuda_dev):
     H = np.loadtxt(__import__("os").path.join(__import__("os").path.dirname(__file__), "golden", "eq1_H.txt"))
     base = np.where(H == 1, 0, -1).astype(np.int32)
@@ -127,10 +143,11 @@ def test_eq1_code_z1_and_extreme_shifts(cuda_dev):
         oc = O.QCCode(B, Z)
         L = (1.5 + 2.0 * rng.standard_normal((37, code.N))).astype(np.float32)
         for T in (1, 3):
-            bits, iters, app = ldpc.decode(code, ldpc.params_for("flood_f32", max_iter=T, early_exit=0),
-                                           torch.from_numpy(L).to(cuda_dev), app=True)
-            ref, _, _ = oc.spa_flood(L, T, early_exit=False)
-            assert rel_err(app.cpu().numpy(), ref).max() <= FP32_TOL
+            for form in ("flood_f32", "stream_f32"):
+                bits, iters, app = ldpc.decode(code, ldpc.params_for(form, max_iter=T, early_exit=0),
+                                               torch.from_numpy(L).to(cuda_dev), app=True)
+                ref, _, _ = oc.spa_flood(L, T, early_exit=False)
+                assert rel_err(app.cpu().numpy(), ref).max() <= FP32_TOL
 
 
 def test_multistream_host_path_matches_device_path(cuda_dev):

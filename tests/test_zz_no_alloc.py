@@ -26,7 +26,7 @@ def _decode_static(code, p, x, dev):
     return bits.cpu().numpy(), iters.cpu().numpy(), app.cpu().numpy()
 
 
-@pytest.mark.parametrize("form", ["flood_f32", "flood_f16"])
+@pytest.mark.parametrize("form", ["flood_f32", "flood_f16", "stream_f32"])
 def test_static_scratch_matches_allocating_entry_point(cuda_dev, form):
     B, Z = I.load_code("qc12x24_z81_s2")
     code = ldpc.Code(B, Z)
@@ -44,9 +44,10 @@ def test_static_scratch_matches_allocating_entry_point(cuda_dev, form):
 
 
 def test_static_scratch_rejects_batches_beyond_the_array(cuda_dev):
+    # the streaming kernels' scratch grows with the batch (tiles of 128 codewords)
     B, Z = I.load_code("qc12x24_z81_s2")
     code = ldpc.Code(B, Z)
-    p = ldpc.params_for("flood_f32")
+    p = ldpc.params_for("stream_f32")
     assert ldpc.ldpc_workspace_size(code.handle, p, 896) <= ldpc.LDPC_STATIC_SCRATCH_BYTES
     assert ldpc.ldpc_workspace_size(code.handle, p, 897) > ldpc.LDPC_STATIC_SCRATCH_BYTES
     x = torch.zeros((897, code.N), device=cuda_dev)
