@@ -55,7 +55,8 @@ typedef enum {
                             /* library expm1f/log1pf phi, state streamed through HBM)        */
     LDPC_IMPL_STREAMING = 2 /* flooding with all state streamed through HBM in the          */
                             /* codeword-interleaved layout (check-node and variable-node    */
-                            /* kernels per iteration)                                        */
+                            /* kernels per iteration); layered min-sum with a fixed group of */
+                            /* codewords per CTA instead of persistent refilled slots        */
 } ldpc_impl;
 
 /* Opaque code object (library-owned, immutable after creation, usable from any thread). */

@@ -66,25 +66,54 @@ __device__ __forceinline__ float s_phi_out(float s2)
     return s_lg2((1.0f + t) * s_rcp(den)) * kSLn2;
 }
 
-template <typename T>
-__device__ __forceinline__ float msg_ld(const T *p);
+// V consecutive slots share each shared-memory element group: APP and R are laid out
+// [slot group][node][V], so one 64-bit (V = 2) shared access serves both codewords of a
+// thread and the index arithmetic of an edge is paid once for V codewords.
+template <typename T, int V>
+struct SMsg;
 template <>
-__device__ __forceinline__ float msg_ld<float>(const float *p) { return *p; }
+struct SMsg<float, 1> {
+    static __device__ __forceinline__ void ld(const float *p, float (&x)[1]) { x[0] = *p; }
+    static __device__ __forceinline__ void st(float *p, const float (&x)[1]) { *p = x[0]; }
+};
 template <>
-__device__ __forceinline__ float msg_ld<__half>(const __half *p) { return __half2float(*p); }
-template <typename T>
-__device__ __forceinline__ void msg_st(T *p, float v);
+struct SMsg<float, 2> {
+    static __device__ __forceinline__ void ld(const float *p, float (&x)[2])
+    {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        x[0] = v.x;
+        x[1] = v.y;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&x)[2])
+    {
+        *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+    }
+};
 template <>
-__device__ __forceinline__ void msg_st<float>(float *p, float v) { *p = v; }
+struct SMsg<__half, 1> {
+    static __device__ __forceinline__ void ld(const __half *p, float (&x)[1]) { x[0] = __half2float(*p); }
+    static __device__ __forceinline__ void st(__half *p, const float (&x)[1]) { *p = __float2half_rn(x[0]); }
+};
 template <>
-__device__ __forceinline__ void msg_st<__half>(__half *p, float v) { *p = __float2half_rn(v); }
+struct SMsg<__half, 2> {
+    static __device__ __forceinline__ void ld(const __half *p, float (&x)[2])
+    {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        x[0] = v.x;
+        x[1] = v.y;
+    }
+    static __device__ __forceinline__ void st(__half *p, const float (&x)[2])
+    {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(x[0], x[1]);
+    }
+};
 
 struct SlotArgs {
     const float *llr;
     int64_t n_cw;
-    int C;             // slots per CTA
-    int strideA;       // floats per slot APP row (N rounded up)
-    int strideR;       // messages per slot R row (E rounded up)
+    int C;             // slots per CTA (a multiple of V)
+    int strideA;       // nodes per slot-group APP block (N rounded up)
+    int strideR;       // edges per slot-group R block (E rounded up)
     int max_iter, early_exit;
     float X;
     uint8_t *bits;
@@ -99,170 +128,237 @@ __host__ __device__ inline size_t slot_tables_bytes(const CodeDev &h)
     return (size_t)(2 * h.nnz + h.mb + 1 + h.nb + 1) * sizeof(int32_t);
 }
 
-template <int DMAX, typename MsgT>
-__global__ void __launch_bounds__(1024, 1) k_flood_slots(const CodeDev *__restrict__ cd, SlotArgs a)
+template <int V>
+constexpr int slot_threads_max() { return V == 2 ? 512 : 1024; }
+
+template <int DMAX, int V, typename MsgT>
+__global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const CodeDev *__restrict__ cd, SlotArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = cd->N, Z = cd->Z, mb = cd->mb, nb = cd->nb, nnz = cd->nnz;
-    const int C = a.C;
+    const int C = a.C, G = a.C / V;
     float *APPs = reinterpret_cast<float *>(smem);
-    MsgT *Rs = reinterpret_cast<MsgT *>(APPs + (size_t)C * a.strideA);
-    int32_t *t_ent = reinterpret_cast<int32_t *>(Rs + (size_t)C * a.strideR);
+    MsgT *Rs = reinterpret_cast<MsgT *>(APPs + (size_t)G * a.strideA * V);
+    int32_t *t_ent = reinterpret_cast<int32_t *>(Rs + (size_t)G * a.strideR * V);
     int32_t *t_colent = t_ent + nnz;
     int32_t *t_rowptr = t_colent + nnz;
     int32_t *t_colptr = t_rowptr + mb + 1;
     int32_t *bad = t_colptr + nb + 1;     // [C] an unsatisfied check was seen this round
     int64_t *fresh = reinterpret_cast<int64_t *>(((uintptr_t)(bad + C) + 7) & ~(uintptr_t)7);  // [C] next codeword
 
+    // tables, pre-scaled: t_ent[b] = (s << 16) | (j * Z) for block b; t_colent[i] = b * Z
+    // for the i-th block of the column lists.  Messages are stored at the variable's
+    // position inside its block: edge (b, r) of check row r lives at b * Z + (r + s) mod Z,
+    // so the check-node phase computes the wrap once for both addresses and the
+    // variable-node phase, summing column position r of block column j, reads b * Z + r.
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < nnz; i += nth) {
-        t_ent[i] = cd->ent[i];
-        t_colent[i] = cd->colent[i];
+        const int e = cd->ent[i];
+        t_ent[i] = ((e & 0xffff) << 16) | ((e >> 16) * Z);
+        t_colent[i] = (cd->colent[i] >> 16) * Z;
     }
     for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
     for (int i = tid; i <= nb; i += nth) t_colptr[i] = cd->colptr[i];
-    const int c = tid / Z, r = tid - (tid / Z) * Z;
-    const bool mine = c < C;
+    const int g = tid / Z, r = tid - (tid / Z) * Z;
+    const bool mine = g < G;
     if (mine && r == 0) {
-        const unsigned long long k = atomicAdd(a.next, 1ull);
-        fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
-        bad[c] = 0;
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            const unsigned long long k = atomicAdd(a.next, 1ull);
+            fresh[g * V + v] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+            bad[g * V + v] = 0;
+        }
     }
     __syncthreads();
 
-    float *A = APPs + (size_t)(mine ? c : 0) * a.strideA;
-    MsgT *Rc = Rs + (size_t)(mine ? c : 0) * a.strideR;
+    float *A = APPs + (size_t)(mine ? g : 0) * a.strideA * V;
+    MsgT *Rc = Rs + (size_t)(mine ? g : 0) * a.strideR * V;
     const float X = a.X, Xb = a.X * kSLog2e;
     constexpr uint32_t kSign = 0x80000000u;
-    int64_t cw = -1;  // codeword in this thread's slot (identical across the slot's threads)
-    int t = 0;        // iterations completed on it
+    int64_t cw[V];  // codeword in each of this thread's slots (identical across the slot group's threads)
+    int t[V];       // iterations completed on it
 
-    // load a new codeword into this thread's columns: APP = L (+0 for -0), R = 0
-    auto refill = [&](int64_t k) {
+    // load a new codeword into slot v, this thread's columns: APP = L (+0 for -0), R = 0
+    auto refill = [&](int v, int64_t k) {
         const float *Lr = a.llr + k * N;
         for (int j0 = 0; j0 < nb; j0 += 8) {
-            float v[8];
+            float x[8];
 #pragma unroll
             for (int u = 0; u < 8; u++)
-                if (j0 + u < nb) v[u] = __ldg(Lr + (j0 + u) * Z + r);
+                if (j0 + u < nb) x[u] = __ldg(Lr + (j0 + u) * Z + r);
 #pragma unroll
             for (int u = 0; u < 8; u++)
-                if (j0 + u < nb) A[(j0 + u) * Z + r] = v[u] + 0.0f;
+                if (j0 + u < nb) A[((j0 + u) * Z + r) * V + v] = x[u] + 0.0f;
         }
-        for (int b = 0; b < nnz; b++) msg_st<MsgT>(Rc + b * Z + r, 0.0f);
+        for (int b = 0; b < nnz; b++) {
+            if constexpr (sizeof(MsgT) == 2)
+                Rc[(b * Z + r) * V + v] = __float2half_rn(0.0f);
+            else
+                Rc[(b * Z + r) * V + v] = 0.0f;
+        }
     };
 
-    if (mine) {
-        cw = fresh[c];
-        if (cw >= 0) refill(cw);
+    bool any = false;
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        cw[v] = mine ? fresh[g * V + v] : -1;
+        t[v] = 0;
+        if (cw[v] >= 0) refill(v, cw[v]);
+        any |= cw[v] >= 0;
     }
-    if (!__syncthreads_or(mine && cw >= 0)) return;
+    if (!__syncthreads_or(any)) return;
 
     for (;;) {
-        const bool busy = mine && cw >= 0;
-        // ---------------- check-node phase
-        if (busy) {
-            uint32_t parity_bad = 0;
+        // ---------------- check-node phase: row r of every block row, all V slots at once
+        if (any) {
+            uint32_t pbad[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) pbad[v] = 0;
             for (int l = 0; l < mb; l++) {
                 const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
-                float av[DMAX];
-                float S = 0.0f, amax = 0.0f;
-                uint32_t sg = 0, par = 0;
+                float av[DMAX][V];
+                uint32_t sg[V], par[V];
+#pragma unroll
+                for (int v = 0; v < V; v++) sg[v] = par[v] = 0;
+                int xo[DMAX];  // wrapped position (r + s) mod Z of each edge
 #pragma unroll
                 for (int k = 0; k < DMAX; k++) {
                     if (k < dc) {
                         const int ent = t_ent[b0 + k];
-                        int x = r + (ent & 0xffff);
+                        int x = r + (ent >> 16);
                         x -= (x >= Z) ? Z : 0;
-                        const float ap = A[(ent >> 16) * Z + x];
-                        const float q = ap - msg_ld<MsgT>(Rc + (b0 + k) * Z + r);
-                        par ^= __float_as_uint(ap);
-                        const float mag = fminf(s_psi_in(fminf(fabsf(q), X)), Xb);
-                        S += mag;
-                        amax = fmaxf(amax, mag);
-                        const uint32_t qs = __float_as_uint(q) & kSign;
-                        sg ^= qs;
-                        av[k] = __uint_as_float(__float_as_uint(mag) | qs);
+                        xo[k] = x;
+                        float ap[V], rv[V];
+                        SMsg<float, V>::ld(A + ((ent & 0xffff) + x) * V, ap);
+                        SMsg<MsgT, V>::ld(Rc + ((b0 + k) * Z + x) * V, rv);
+#pragma unroll
+                        for (int v = 0; v < V; v++) {
+                            const float q = ap[v] - rv[v];
+                            par[v] ^= __float_as_uint(ap[v]);
+                            const float mag = fminf(s_psi_in(fminf(fabsf(q), X)), Xb);
+                            const uint32_t qs = __float_as_uint(q) & kSign;
+                            sg[v] ^= qs;
+                            av[k][v] = __uint_as_float(__float_as_uint(mag) | qs);
+                        }
                     }
                 }
-                float Sx = 0.0f;
+                // exclusive sums from suffix and prefix sums of |a| (no cancellation)
+                float sf[DMAX + 1][V];
 #pragma unroll
-                for (int k = 0; k < DMAX; k++)
-                    if (k < dc) Sx += (fabsf(av[k]) == amax) ? 0.0f : fabsf(av[k]);
-                const float sx = (amax > 0.5f * S) ? Sx : S - amax;
+                for (int v = 0; v < V; v++) sf[DMAX][v] = 0.0f;
+#pragma unroll
+                for (int k = DMAX - 1; k >= 0; k--)
+#pragma unroll
+                    for (int v = 0; v < V; v++) sf[k][v] = (k < dc) ? sf[k + 1][v] + fabsf(av[k][v]) : 0.0f;
+                float pre[V];
+#pragma unroll
+                for (int v = 0; v < V; v++) pre[v] = 0.0f;
 #pragma unroll
                 for (int k = 0; k < DMAX; k++) {
                     if (k < dc) {
-                        const float ak = fabsf(av[k]);
-                        const float ex = (ak == amax) ? sx : S - ak;
-                        const float mag = fminf(s_phi_out(ex), X);
-                        const float rn = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k]) ^ sg) & kSign));
-                        msg_st<MsgT>(Rc + (b0 + k) * Z + r, rn);
+                        float out[V];
+#pragma unroll
+                        for (int v = 0; v < V; v++) {
+                            const float mag = fminf(s_phi_out(pre[v] + sf[k + 1][v]), X);
+                            pre[v] += fabsf(av[k][v]);
+                            out[v] = __uint_as_float(__float_as_uint(mag) |
+                                                     ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
+                        }
+                        SMsg<MsgT, V>::st(Rc + ((b0 + k) * Z + xo[k]) * V, out);
                     }
                 }
-                parity_bad |= par;
+#pragma unroll
+                for (int v = 0; v < V; v++) pbad[v] |= par[v];
             }
-            if (parity_bad & kSign) bad[c] = 1;
+#pragma unroll
+            for (int v = 0; v < V; v++)
+                if (cw[v] >= 0 && (pbad[v] & kSign)) bad[g * V + v] = 1;
         }
         __syncthreads();
 
         // ---------------- decision, variable-node phase, output
-        bool done = false;
-        if (busy) {
-            const bool converged = t >= 1 && a.early_exit && bad[c] == 0;
-            if (!converged) {
-                const float *Lr = a.llr + cw * N;
-                for (int j0 = 0; j0 < nb; j0 += 8) {
-                    float v[8];
+        bool done[V];
+        if (any) {
+            bool act[V];
+            bool anyact = false;
 #pragma unroll
-                    for (int u = 0; u < 8; u++)
-                        if (j0 + u < nb) v[u] = __ldg(Lr + (j0 + u) * Z + r);
+            for (int v = 0; v < V; v++) {
+                const bool conv = cw[v] >= 0 && t[v] >= 1 && a.early_exit && bad[g * V + v] == 0;
+                act[v] = cw[v] >= 0 && !conv;
+                done[v] = conv;
+                anyact |= act[v];
+            }
+            if (anyact) {
+                for (int j0 = 0; j0 < nb; j0 += 4) {
+                    float lv[4][V];
 #pragma unroll
-                    for (int u = 0; u < 8; u++) {
+                    for (int u = 0; u < 4; u++)
+#pragma unroll
+                        for (int v = 0; v < V; v++)
+                            if (j0 + u < nb && act[v]) lv[u][v] = __ldg(a.llr + cw[v] * N + (j0 + u) * Z + r);
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
                         const int j = j0 + u;
                         if (j < nb) {
-                            float s = v[u];
+                            float sacc[V];
+#pragma unroll
+                            for (int v = 0; v < V; v++) sacc[v] = lv[u][v];
                             const int i1 = t_colptr[j + 1];
                             for (int i = t_colptr[j]; i < i1; i++) {
-                                const int ce = t_colent[i];
-                                int rr = r - (ce & 0xffff);
-                                rr += (rr < 0) ? Z : 0;
-                                s += msg_ld<MsgT>(Rc + (ce >> 16) * Z + rr);
+                                float rv[V];
+                                SMsg<MsgT, V>::ld(Rc + (t_colent[i] + r) * V, rv);
+#pragma unroll
+                                for (int v = 0; v < V; v++) sacc[v] += rv[v];
                             }
-                            A[j * Z + r] = s + 0.0f;  // -0 -> +0: the sign bit is the hard decision
+#pragma unroll
+                            for (int v = 0; v < V; v++)
+                                if (act[v]) A[(j * Z + r) * V + v] = sacc[v] + 0.0f;  // -0 -> +0: sign bit = decision
                         }
                     }
                 }
-                t++;
             }
-            done = converged || t >= a.max_iter;
-            if (done) {
-                uint8_t *Bo = a.bits + cw * N;
-                float *Ao = a.app_out ? a.app_out + cw * N : nullptr;
-                for (int j = 0; j < nb; j++) {
-                    const float v = A[j * Z + r];
-                    Bo[j * Z + r] = v < 0.0f ? 1 : 0;
-                    if (Ao) Ao[j * Z + r] = v;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                if (act[v]) {
+                    t[v]++;
+                    done[v] = t[v] >= a.max_iter;
                 }
-                if (r == 0) {
-                    a.iters[cw] = t;
-                    const unsigned long long k = atomicAdd(a.next, 1ull);
-                    fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+                if (done[v]) {
+                    uint8_t *Bo = a.bits + cw[v] * N;
+                    float *Ao = a.app_out ? a.app_out + cw[v] * N : nullptr;
+                    for (int j = 0; j < nb; j++) {
+                        const float x = A[(j * Z + r) * V + v];
+                        Bo[j * Z + r] = x < 0.0f ? 1 : 0;
+                        if (Ao) Ao[j * Z + r] = x;
+                    }
+                    if (r == 0) {
+                        a.iters[cw[v]] = t[v];
+                        const unsigned long long k = atomicAdd(a.next, 1ull);
+                        fresh[g * V + v] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+                    }
                 }
             }
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; v++) done[v] = false;
         }
         __syncthreads();
 
         // ---------------- refill finished slots
-        if (busy) {
-            if (r == 0) bad[c] = 0;
-            if (done) {
-                cw = fresh[c];
-                t = 0;
-                if (cw >= 0) refill(cw);
+        any = false;
+        if (mine) {
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                if (r == 0) bad[g * V + v] = 0;
+                if (done[v]) {
+                    cw[v] = fresh[g * V + v];
+                    t[v] = 0;
+                    if (cw[v] >= 0) refill(v, cw[v]);
+                }
+                any |= cw[v] >= 0;
             }
         }
-        if (!__syncthreads_or(mine && cw >= 0)) break;
+        if (!__syncthreads_or(any)) break;
     }
 }
 
@@ -298,36 +394,54 @@ static size_t slot_bytes(const CodeDev &h, int msg)
     return sa + sr + sizeof(int32_t) + sizeof(int64_t);
 }
 
+#ifndef LDPC_SLOTS_V
+#define LDPC_SLOTS_V 2  // codewords per thread in the slot decoder (1 or 2)
+#endif
+
 static size_t slots_smem(const CodeDev &h, int msg, int C)
 {
     return (size_t)C * slot_bytes(h, msg) + slot_tables_bytes(h) + 64;
 }
 
-// slots per CTA (0 if one slot does not fit on chip)
-int slots_per_cta(const CodeDev &h, int msg, size_t smem_limit)
+// slots per CTA (0 if one slot does not fit on chip); *v gets the codewords per thread
+int slots_per_cta(const CodeDev &h, int msg, size_t smem_limit, int *v = nullptr)
 {
     if (h.dc_max > 32) return 0;
-    int C = (int)(1024 / h.Z);
-    while (C > 0 && slots_smem(h, msg, C) > smem_limit) C--;
-    return C;
+    // single slots: as many as fit; paired slots (two codewords per thread) when pairing
+    // loses no slot
+    int C1 = (int)(slot_threads_max<1>() / h.Z);
+    while (C1 > 0 && slots_smem(h, msg, C1) > smem_limit) C1--;
+    int C2 = (int)(slot_threads_max<2>() / h.Z) * 2;
+    while (C2 > 0 && slots_smem(h, msg, C2) > smem_limit) C2--;
+    C2 -= C2 % 2;
+    const bool pair = LDPC_SLOTS_V == 2 && C2 >= 2 && C2 >= C1;
+    if (v) *v = pair ? 2 : 1;
+    return pair ? C2 : C1;
 }
 
 int slots_supported(const CodeDev &h, int msg) { return slots_per_cta(h, msg, 227 * 1024) > 0; }
 
-template <int DMAX, typename MsgT>
+template <int DMAX, int V, typename MsgT>
 static cudaError_t launch_slots(const CodeDev &h, const CodeDev *d, SlotArgs a, cudaStream_t s)
 {
     const size_t sm = slots_smem(h, sizeof(MsgT) == 2 ? LDPC_MSG_F16 : LDPC_MSG_F32, a.C);
-    cudaError_t e = cudaFuncSetAttribute(k_flood_slots<DMAX, MsgT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_flood_slots<DMAX, V, MsgT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
-    const int threads = ((a.C * h.Z + 31) / 32) * 32;
+    const int threads = ((a.C / V * h.Z + 31) / 32) * 32;
     int64_t ctas = sm_count();
     const int64_t need = (a.n_cw + a.C - 1) / a.C;
     if (need < ctas) ctas = need;
     LaunchScope ls(F_SLOTS, s);
-    k_flood_slots<DMAX, MsgT><<<(unsigned)ctas, threads, sm, s>>>(d, a);
+    k_flood_slots<DMAX, V, MsgT><<<(unsigned)ctas, threads, sm, s>>>(d, a);
     return cudaGetLastError();
+}
+
+template <int DMAX, typename MsgT>
+static cudaError_t launch_slots_v(const CodeDev &h, const CodeDev *d, SlotArgs a, int V, cudaStream_t s)
+{
+    if (V == 2) return launch_slots<DMAX, 2, MsgT>(h, d, a, s);
+    return launch_slots<DMAX, 1, MsgT>(h, d, a, s);
 }
 
 cudaError_t slots_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p, const float *llr,
@@ -337,7 +451,8 @@ cudaError_t slots_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_p
     SlotArgs a;
     a.llr = llr;
     a.n_cw = n_cw;
-    a.C = slots_per_cta(h, p.msg, (size_t)max_smem_optin());
+    int V = 1;
+    a.C = slots_per_cta(h, p.msg, (size_t)max_smem_optin(), &V);
     if (a.C < 1) return cudaErrorInvalidValue;
     a.strideA = (h.N + 3) & ~3;
     a.strideR = (h.E + 7) & ~7;
@@ -350,9 +465,10 @@ cudaError_t slots_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_p
     a.next = static_cast<unsigned long long *>(counter);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    if (h.dc_max <= 8) return f16 ? launch_slots<8, __half>(h, d, a, s) : launch_slots<8, float>(h, d, a, s);
-    if (h.dc_max <= 16) return f16 ? launch_slots<16, __half>(h, d, a, s) : launch_slots<16, float>(h, d, a, s);
-    return f16 ? launch_slots<32, __half>(h, d, a, s) : launch_slots<32, float>(h, d, a, s);
+    if (h.dc_max <= 8) return f16 ? launch_slots_v<8, __half>(h, d, a, V, s) : launch_slots_v<8, float>(h, d, a, V, s);
+    if (h.dc_max <= 16)
+        return f16 ? launch_slots_v<16, __half>(h, d, a, V, s) : launch_slots_v<16, float>(h, d, a, V, s);
+    return f16 ? launch_slots_v<32, __half>(h, d, a, V, s) : launch_slots_v<32, float>(h, d, a, V, s);
 }
 
 }  // namespace ldpc

@@ -170,6 +170,168 @@ __global__ void __launch_bounds__(512) k_layered_nms(const CodeDev *__restrict__
         if (cw0 + cc < a.n_cw) a.iters[cw0 + cc] = its[cc];
 }
 
+// ------------------------------------------------------------------ slot decoder
+
+// Persistent form: one CTA per SM holds C codeword slots (APP and R of each in shared
+// memory, R at the variable's position inside its block, edge (b, row r) at b*Z + (r+s) mod Z)
+// and runs the layers of all slots in lockstep, each slot at its own iteration.  After every
+// full iteration each slot's hard decisions are checked against all its checks; a slot that
+// converged (or reached max_iter) writes its outputs and takes the next codeword from the
+// global work counter, so no thread idles while a slower codeword of the same CTA decodes.
+struct LayeredSlotArgs {
+    const void *llr;
+    int llr_type;
+    float scale;
+    int64_t n_cw;
+    int C, strideA, strideR;
+    int max_iter, early_exit, alpha_num, alpha_shift, msg_sat, app_sat;
+    uint8_t *bits;
+    int32_t *iters;
+    float *app_out;
+    unsigned long long *next;
+};
+
+template <int DMAX>
+__global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__restrict__ cd, LayeredSlotArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = cd->N, Z = cd->Z, mb = cd->mb, nb = cd->nb, nnz = cd->nnz;
+    const int C = a.C;
+    int8_t *APPs = reinterpret_cast<int8_t *>(smem);
+    int8_t *Rs = APPs + (size_t)C * a.strideA;
+    int32_t *t_ent = reinterpret_cast<int32_t *>(Rs + (size_t)C * a.strideR);  // (s << 16) | j*Z
+    int32_t *t_rowptr = t_ent + nnz;
+    int32_t *bad = t_rowptr + mb + 1;
+    int64_t *fresh = reinterpret_cast<int64_t *>(((uintptr_t)(bad + C) + 7) & ~(uintptr_t)7);
+
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int i = tid; i < nnz; i += nth) {
+        const int e = cd->ent[i];
+        t_ent[i] = ((e & 0xffff) << 16) | ((e >> 16) * Z);
+    }
+    for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
+    const int c = tid / Z, r = tid - (tid / Z) * Z;
+    const bool mine = c < C;
+    if (mine && r == 0) {
+        const unsigned long long k = atomicAdd(a.next, 1ull);
+        fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+        bad[c] = 0;
+    }
+    __syncthreads();
+    int8_t *A = APPs + (size_t)(mine ? c : 0) * a.strideA;
+    int8_t *Rc = Rs + (size_t)(mine ? c : 0) * a.strideR;
+
+    auto refill = [&](int64_t k) {
+        for (int j = 0; j < nb; j++) {
+            const int64_t i = k * N + j * Z + r;
+            int q;
+            if (a.llr_type == LDPC_LLR_I8) {
+                q = sat_i(static_cast<const int8_t *>(a.llr)[i], a.msg_sat);
+            } else {
+                const float rr = rintf(__fmul_rn(a.scale, __ldg(static_cast<const float *>(a.llr) + i)));
+                q = rr > (float)a.msg_sat ? a.msg_sat : (rr < -(float)a.msg_sat ? -a.msg_sat : (int)rr);
+            }
+            A[j * Z + r] = (int8_t)q;
+        }
+        for (int b = 0; b < nnz; b++) Rc[b * Z + r] = 0;
+    };
+
+    int64_t cw = mine ? fresh[c] : -1;
+    int t = 0;
+    if (cw >= 0) refill(cw);
+    if (!__syncthreads_or(cw >= 0)) return;
+
+    for (;;) {
+        const bool busy = cw >= 0;
+        for (int l = 0; l < mb; l++) {
+            if (busy) {
+                const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
+                int qx[DMAX];  // (wrapped position << 8) | (Q & 0xff): one register per edge
+                int min1 = 0x7fffffff, min2 = 0x7fffffff, arg = -1;
+                unsigned S = 0;
+#pragma unroll
+                for (int k = 0; k < DMAX; k++) {
+                    if (k < dc) {
+                        const int ent = t_ent[b0 + k];
+                        int x = r + (ent >> 16);
+                        x -= (x >= Z) ? Z : 0;
+                        const int qq = sat_i((int)A[(ent & 0xffff) + x] - (int)Rc[(b0 + k) * Z + x], a.msg_sat);
+                        const int mag = qq < 0 ? -qq : qq;
+                        if (mag < min1) {
+                            min2 = min1;
+                            min1 = mag;
+                            arg = k;
+                        } else if (mag < min2) {
+                            min2 = mag;
+                        }
+                        S ^= qq < 0 ? 1u : 0u;
+                        qx[k] = (x << 8) | (qq & 0xff);
+                    }
+                }
+                const int m1 = (a.alpha_num * min1) >> a.alpha_shift;
+                const int m2 = (a.alpha_num * min2) >> a.alpha_shift;
+#pragma unroll
+                for (int k = 0; k < DMAX; k++) {
+                    if (k < dc) {
+                        const int qq = (int)(int8_t)(qx[k] & 0xff);
+                        const int x = qx[k] >> 8;
+                        const int magp = (k == arg) ? m2 : m1;
+                        const int rn = (S ^ (qq < 0 ? 1u : 0u)) ? -magp : magp;
+                        Rc[(b0 + k) * Z + x] = (int8_t)rn;
+                        A[(t_ent[b0 + k] & 0xffff) + x] = (int8_t)sat_i(qq + rn, a.app_sat);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (busy) t++;
+        // syndrome of the hard decisions: row r of every layer
+        if (busy && a.early_exit) {
+            unsigned par_any = 0;
+            for (int l = 0; l < mb; l++) {
+                unsigned par = 0;
+                for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++) {
+                    const int ent = t_ent[b];
+                    int x = r + (ent >> 16);
+                    x -= (x >= Z) ? Z : 0;
+                    par ^= A[(ent & 0xffff) + x] < 0 ? 1u : 0u;
+                }
+                par_any |= par;
+            }
+            if (par_any) bad[c] = 1;
+        }
+        __syncthreads();
+        bool done = false;
+        if (busy) {
+            done = (a.early_exit && bad[c] == 0) || t >= a.max_iter;
+            if (done) {
+                uint8_t *Bo = a.bits + cw * N;
+                float *Ao = a.app_out ? a.app_out + cw * N : nullptr;
+                for (int j = 0; j < nb; j++) {
+                    const int v = A[j * Z + r];
+                    Bo[j * Z + r] = v < 0 ? 1 : 0;
+                    if (Ao) Ao[j * Z + r] = (float)v;
+                }
+                if (r == 0) {
+                    a.iters[cw] = t;
+                    const unsigned long long k = atomicAdd(a.next, 1ull);
+                    fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+                }
+            }
+        }
+        __syncthreads();
+        if (busy) {
+            if (r == 0) bad[c] = 0;
+            if (done) {
+                cw = fresh[c];
+                t = 0;
+                if (cw >= 0) refill(cw);
+            }
+        }
+        if (!__syncthreads_or(cw >= 0)) break;
+    }
+}
+
 static int pick_C(const CodeDev &h) { return h.Z >= 512 ? 1 : (512 / h.Z); }
 
 static size_t layered_smem(const CodeDev &h, int C)
@@ -193,6 +355,69 @@ static cudaError_t launch_layered(const CodeDev &h, const CodeDev *d, const Laye
     LaunchScope ls(F_LAYERED, s);
     k_layered_nms<DMAX><<<blocks, threads, sm, s>>>(d, a);
     return cudaGetLastError();
+}
+
+static size_t lslots_smem(const CodeDev &h, int C)
+{
+    return (size_t)C * (((h.N + 15) & ~15) + ((h.E + 15) & ~15) + sizeof(int32_t) + sizeof(int64_t)) +
+           (size_t)(h.nnz + h.mb + 1) * sizeof(int32_t) + 64;
+}
+
+int layered_slots_per_cta(const CodeDev &h)
+{
+    if (h.dc_max > 32 || h.N >= 65536) return 0;
+    int C = 1024 / h.Z;
+    while (C > 0 && lslots_smem(h, C) > 200 * 1024) C--;
+    return C;
+}
+
+template <int DMAX>
+static cudaError_t launch_lslots(const CodeDev &h, const CodeDev *d, const LayeredSlotArgs &a, cudaStream_t s)
+{
+    const size_t sm = lslots_smem(h, a.C);
+    cudaError_t e = cudaFuncSetAttribute(k_layered_slots<DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t ctas = nsm;
+    const int64_t need = (a.n_cw + a.C - 1) / a.C;
+    if (need < ctas) ctas = need;
+    const int threads = ((a.C * h.Z + 31) / 32) * 32;
+    LaunchScope ls(F_LAYERED, s);
+    k_layered_slots<DMAX><<<(unsigned)ctas, threads, sm, s>>>(d, a);
+    return cudaGetLastError();
+}
+
+cudaError_t layered_slots_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p, const void *llr,
+                                 int llr_type, int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out,
+                                 void *counter, cudaStream_t s)
+{
+    LayeredSlotArgs a;
+    a.llr = llr;
+    a.llr_type = llr_type;
+    a.scale = p.llr_scale;
+    a.n_cw = n_cw;
+    a.C = layered_slots_per_cta(h);
+    if (a.C < 1) return cudaErrorInvalidValue;
+    a.strideA = (h.N + 15) & ~15;
+    a.strideR = (h.E + 15) & ~15;
+    a.max_iter = p.max_iter;
+    a.early_exit = p.early_exit;
+    a.alpha_num = p.nms_alpha_num;
+    a.alpha_shift = p.nms_alpha_shift;
+    a.msg_sat = p.msg_sat;
+    a.app_sat = p.app_sat;
+    a.bits = bits;
+    a.iters = iters;
+    a.app_out = app_out;
+    a.next = static_cast<unsigned long long *>(counter);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    if (h.dc_max <= 8) return launch_lslots<8>(h, d, a, s);
+    if (h.dc_max <= 16) return launch_lslots<16>(h, d, a, s);
+    if (h.dc_max <= 24) return launch_lslots<24>(h, d, a, s);
+    return launch_lslots<32>(h, d, a, s);
 }
 
 cudaError_t layered_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p, const void *llr,

@@ -235,7 +235,7 @@ static ldpc_status check_params(const ldpc_code *c, const ldpc_decode_params *p,
     }
     if (p->sched == LDPC_SCHED_LAYERED && p->algo == LDPC_ALGO_NMS) {
         if (p->msg != LDPC_MSG_I8) return fail(LDPC_ENOTSUP, "layered min-sum stores I8 messages");
-        if (p->impl != LDPC_IMPL_AUTO) return fail(LDPC_ENOTSUP, "no plain layered implementation");
+        if (p->impl == LDPC_IMPL_PLAIN) return fail(LDPC_ENOTSUP, "no plain layered implementation");
         if (p->msg_sat < 1 || p->msg_sat > 127 || p->app_sat < p->msg_sat || p->app_sat > 127)
             return fail(LDPC_EINVAL, "need 1 <= msg_sat <= app_sat <= 127");
         if (p->nms_alpha_num < 1 || p->nms_alpha_shift < 0 || p->nms_alpha_shift > 16 ||
@@ -259,9 +259,18 @@ static bool use_slots(const ldpc_code *c, const ldpc_decode_params *p)
     return p->sched == LDPC_SCHED_FLOODING && p->impl == LDPC_IMPL_AUTO && ldpc::slots_supported(c->host, p->msg);
 }
 
+// The layered min-sum runs as persistent slots (work counter in the workspace) unless
+// LDPC_IMPL_STREAMING asks for the one-CTA-per-group kernel, which needs no workspace.
+static bool use_layered_slots(const ldpc_code *c, const ldpc_decode_params *p)
+{
+    return p->sched == LDPC_SCHED_LAYERED && p->impl == LDPC_IMPL_AUTO && ldpc::layered_slots_per_cta(c->host) > 0;
+}
+
 static size_t ws_bytes(const ldpc_code *c, const ldpc_decode_params *p, int64_t n_cw)
 {
-    if (p->sched == LDPC_SCHED_LAYERED || n_cw == 0) return 0;
+    if (n_cw == 0) return 0;
+    if (use_layered_slots(c, p)) return ldpc::SLOTS_WS_BYTES;
+    if (p->sched == LDPC_SCHED_LAYERED) return 0;
     if (use_slots(c, p)) return ldpc::SLOTS_WS_BYTES;
     return ldpc::flood_ws_layout(c->host, n_cw, p->msg, nullptr, nullptr);
 }
@@ -287,7 +296,7 @@ ldpc_status ldpc_decode_batch(const ldpc_code *c, const ldpc_decode_params *p, c
     if (!llr || !bits || !iters) return fail(LDPC_EINVAL, "llr, bits and iters must be non-NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;
-    if (p->sched == LDPC_SCHED_LAYERED) {
+    if (p->sched == LDPC_SCHED_LAYERED && !use_layered_slots(c, p)) {
         e = ldpc::layered_decode(c->host, c->dev, *p, llr, llr_type, n_cw, bits, iters, app, s);
         return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "layered decode launch");
     }
@@ -306,7 +315,9 @@ ldpc_status ldpc_decode_batch(const ldpc_code *c, const ldpc_decode_params *p, c
         }
         own = true;
     }
-    if (use_slots(c, p)) {
+    if (use_layered_slots(c, p)) {
+        e = ldpc::layered_slots_decode(c->host, c->dev, *p, llr, llr_type, n_cw, bits, iters, app, ws, s);
+    } else if (use_slots(c, p)) {
         e = ldpc::slots_decode(c->host, c->dev, *p, static_cast<const float *>(llr), n_cw, bits, iters, app, ws, s);
     } else {
         ldpc::FloodWs w;

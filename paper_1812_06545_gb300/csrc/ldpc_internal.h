@@ -60,6 +60,11 @@ cudaError_t layered_decode(const CodeDev &host, const CodeDev *dev, const ldpc_d
                            int llr_type, int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out,
                            cudaStream_t s);
 int layered_supported(const CodeDev &host);
+// Persistent slot form of the layered min-sum (0 slots: code too large for it).
+int layered_slots_per_cta(const CodeDev &host);
+cudaError_t layered_slots_decode(const CodeDev &host, const CodeDev *dev, const ldpc_decode_params &p, const void *llr,
+                                 int llr_type, int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out,
+                                 void *counter, cudaStream_t s);
 
 // On-chip slot decoder for the flooding forms (flood_slots.cu).  counter: 8 bytes of
 // device memory, zeroed on the stream before the launch.

@@ -226,6 +226,8 @@ FORMS = {
     "stream_f32": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F32, impl=LDPC_IMPL_STREAMING),
     "stream_f16": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F16, impl=LDPC_IMPL_STREAMING),
     "layered_i8": dict(sched=LDPC_SCHED_LAYERED, algo=LDPC_ALGO_NMS, msg=LDPC_MSG_I8),
+    "layered_i8_group": dict(sched=LDPC_SCHED_LAYERED, algo=LDPC_ALGO_NMS, msg=LDPC_MSG_I8,
+                             impl=LDPC_IMPL_STREAMING),
 }
 
 

@@ -23,8 +23,8 @@ def gpu_code(name):
     return _gcodes[name]
 
 
-def run(code, x, dev, **kw):
-    p = ldpc.params_for("layered_i8", **kw)
+def run(code, x, dev, form="layered_i8", **kw):
+    p = ldpc.params_for(form, **kw)
     bits, iters, app = ldpc.decode(code, p, torch.from_numpy(x).to(dev), app=True)
     torch.cuda.synchronize()
     return app.cpu().numpy().astype(np.int32), bits.cpu().numpy(), iters.cpu().numpy()
@@ -38,12 +38,14 @@ def assert_exact(got, ref):
     assert np.array_equal(gb, rb)
 
 
+@pytest.mark.parametrize("form", ["layered_i8", "layered_i8_group"])
 @pytest.mark.parametrize("eb,early", [(4.0, 1), (3.0, 1), (3.0, 0)])
-def test_rate56_bit_exact_int8_input(cuda_dev, eb, early):
+def test_rate56_bit_exact_int8_input(cuda_dev, form, eb, early):
+    # persistent slots (AUTO) and the fixed group-per-CTA kernel, bit-exact alike
     name = "qc4x24_z81_s3"
     _, _, c, L = I.make_frames(name, 1003, eb, 30, 31)
     q = O.quantize(L, 2.0, 31)
-    got = run(gpu_code(name), q, cuda_dev, max_iter=10, early_exit=early)
+    got = run(gpu_code(name), q, cuda_dev, form, max_iter=10, early_exit=early)
     assert_exact(got, oracle_code(name).nms_layered(q, 10, early_exit=bool(early)))
 
 
@@ -61,7 +63,7 @@ def test_fp32_input_quantised_in_kernel(cuda_dev):
 def test_mixed_code_family_bit_exact(cuda_dev, name):
     mb = I.CODE_SPECS[name][0]
     rate = 1 - mb / 24
-    _, _, c, L = I.make_frames(name, 150, 2.0 + 4 * (rate - 0.5), 40, 41)
+    _, _, c, L = I.make_frames(name, 450, 2.0 + 4 * (rate - 0.5), 40, 41)
     q = O.quantize(L, 2.0, 31)
     got = run(gpu_code(name), q, cuda_dev, max_iter=8)
     assert_exact(got, oracle_code(name).nms_layered(q, 8, early_exit=True))
@@ -78,11 +80,12 @@ def test_saturation_parameters(cuda_dev):
         assert_exact(got, ref)
 
 
-def test_large_code_z384(cuda_dev):
+@pytest.mark.parametrize("form", ["layered_i8", "layered_i8_group"])
+def test_large_code_z384(cuda_dev, form):
     name = "qc34x68_z384_s5"
     _, _, c, L = I.make_frames(name, 5, 2.5, 50, 51)
     q = O.quantize(L, 2.0, 31)
-    got = run(gpu_code(name), q, cuda_dev, max_iter=10)
+    got = run(gpu_code(name), q, cuda_dev, form, max_iter=10)
     assert_exact(got, oracle_code(name).nms_layered(q, 10, early_exit=True))
 
 
@@ -95,6 +98,16 @@ def test_eq1_code_z1(cuda_dev):
     q = rng.integers(-31, 32, size=(77, 10)).astype(np.int8)
     got = run(code, q, cuda_dev, max_iter=5)
     assert_exact(got, oc.nms_layered(q, 5, early_exit=True))
+
+
+def test_batch_invariance(cuda_dev):
+    name = "qc4x24_z81_s3"
+    _, _, c, L = I.make_frames(name, 4000, 3.0, 70, 71)
+    q = O.quantize(L, 2.0, 31)
+    ga, gb, gi = run(gpu_code(name), q, cuda_dev, max_iter=10)
+    for i in (0, 11, 12, 1999, 3999):
+        a1, b1, i1 = run(gpu_code(name), q[i:i + 1].copy(), cuda_dev, max_iter=10)
+        assert np.array_equal(a1[0], ga[i]) and i1[0] == gi[i]
 
 
 def test_full_size_sampled(cuda_dev):
