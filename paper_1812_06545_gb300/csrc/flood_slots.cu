@@ -108,6 +108,91 @@ struct SMsg<__half, 2> {
     }
 };
 
+// Degree dispatch: the checks of one block row all have the same degree, so every lane of
+// a warp takes the same branch.  Degrees up to 8 get an exact, guard-free body; larger
+// degrees share buckets of four (edges past the degree are skipped under a uniform guard).
+__host__ __device__ constexpr int next_degree(int d) { return d < 8 ? d + 1 : d + 4; }
+
+// One check of row r for V slots: Q = APP - R over its edges, phi rule, messages written
+// in place (at the variable's position), parity of the APP sign bits accumulated in pbad.
+template <int D, bool EXACT, int V, typename MsgT>
+__device__ __forceinline__ void slot_check(int dc, const int32_t *__restrict__ ent, int bZ, const float *A, MsgT *Rc,
+                                           int r, int Z, float X, float Xb, uint32_t (&pbad)[V])
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    float av[D][V];
+    int xo[D];
+    uint32_t sg[V], par[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) sg[v] = par[v] = 0;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        if (EXACT || k < dc) {
+            const int e = ent[k];
+            int x = r + (e >> 16);
+            x -= (x >= Z) ? Z : 0;
+            xo[k] = x;
+            float ap[V], rv[V];
+            SMsg<float, V>::ld(A + ((e & 0xffff) + x) * V, ap);
+            SMsg<MsgT, V>::ld(Rc + (bZ + k * Z + x) * V, rv);
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const float q = ap[v] - rv[v];
+                par[v] ^= __float_as_uint(ap[v]);
+                const float mag = fminf(s_psi_in(fminf(fabsf(q), X)), Xb);
+                const uint32_t qs = __float_as_uint(q) & kSign;
+                sg[v] ^= qs;
+                av[k][v] = __uint_as_float(__float_as_uint(mag) | qs);
+            }
+        }
+    }
+    // exclusive sums from suffix and prefix sums of |a| (no cancellation)
+    float sf[D + 1][V];
+#pragma unroll
+    for (int v = 0; v < V; v++) sf[D][v] = 0.0f;
+#pragma unroll
+    for (int k = D - 1; k >= 0; k--)
+#pragma unroll
+        for (int v = 0; v < V; v++) sf[k][v] = (EXACT || k < dc) ? sf[k + 1][v] + fabsf(av[k][v]) : 0.0f;
+    float pre[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) pre[v] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        if (EXACT || k < dc) {
+            float out[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const float mag = fminf(s_phi_out(pre[v] + sf[k + 1][v]), X);
+                pre[v] += fabsf(av[k][v]);
+                out[v] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
+            }
+            SMsg<MsgT, V>::st(Rc + (bZ + k * Z + xo[k]) * V, out);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++) pbad[v] |= par[v];
+}
+
+template <int D, int DMAX, int V, typename MsgT>
+__device__ __forceinline__ void slot_check_dispatch(int dc, const int32_t *__restrict__ ent, int bZ, const float *A,
+                                                    MsgT *Rc, int r, int Z, float X, float Xb, uint32_t (&pbad)[V])
+{
+    if constexpr (D >= DMAX) {
+        slot_check<DMAX, false, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+    } else if constexpr (D <= 8) {
+        if (dc == D)
+            slot_check<D, true, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+        else
+            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+    } else {
+        if (dc <= D)
+            slot_check<D, false, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+        else
+            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+    }
+}
+
 struct SlotArgs {
     const float *llr;
     int64_t n_cw;
@@ -129,7 +214,7 @@ __host__ __device__ inline size_t slot_tables_bytes(const CodeDev &h)
 }
 
 template <int V>
-constexpr int slot_threads_max() { return V == 2 ? 512 : 1024; }
+constexpr int slot_threads_max() { return V == 2 ? 512 : 640; }
 
 template <int DMAX, int V, typename MsgT>
 __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const CodeDev *__restrict__ cd, SlotArgs a)
@@ -216,59 +301,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
             for (int v = 0; v < V; v++) pbad[v] = 0;
             for (int l = 0; l < mb; l++) {
                 const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
-                float av[DMAX][V];
-                uint32_t sg[V], par[V];
-#pragma unroll
-                for (int v = 0; v < V; v++) sg[v] = par[v] = 0;
-                int xo[DMAX];  // wrapped position (r + s) mod Z of each edge
-#pragma unroll
-                for (int k = 0; k < DMAX; k++) {
-                    if (k < dc) {
-                        const int ent = t_ent[b0 + k];
-                        int x = r + (ent >> 16);
-                        x -= (x >= Z) ? Z : 0;
-                        xo[k] = x;
-                        float ap[V], rv[V];
-                        SMsg<float, V>::ld(A + ((ent & 0xffff) + x) * V, ap);
-                        SMsg<MsgT, V>::ld(Rc + ((b0 + k) * Z + x) * V, rv);
-#pragma unroll
-                        for (int v = 0; v < V; v++) {
-                            const float q = ap[v] - rv[v];
-                            par[v] ^= __float_as_uint(ap[v]);
-                            const float mag = fminf(s_psi_in(fminf(fabsf(q), X)), Xb);
-                            const uint32_t qs = __float_as_uint(q) & kSign;
-                            sg[v] ^= qs;
-                            av[k][v] = __uint_as_float(__float_as_uint(mag) | qs);
-                        }
-                    }
-                }
-                // exclusive sums from suffix and prefix sums of |a| (no cancellation)
-                float sf[DMAX + 1][V];
-#pragma unroll
-                for (int v = 0; v < V; v++) sf[DMAX][v] = 0.0f;
-#pragma unroll
-                for (int k = DMAX - 1; k >= 0; k--)
-#pragma unroll
-                    for (int v = 0; v < V; v++) sf[k][v] = (k < dc) ? sf[k + 1][v] + fabsf(av[k][v]) : 0.0f;
-                float pre[V];
-#pragma unroll
-                for (int v = 0; v < V; v++) pre[v] = 0.0f;
-#pragma unroll
-                for (int k = 0; k < DMAX; k++) {
-                    if (k < dc) {
-                        float out[V];
-#pragma unroll
-                        for (int v = 0; v < V; v++) {
-                            const float mag = fminf(s_phi_out(pre[v] + sf[k + 1][v]), X);
-                            pre[v] += fabsf(av[k][v]);
-                            out[v] = __uint_as_float(__float_as_uint(mag) |
-                                                     ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
-                        }
-                        SMsg<MsgT, V>::st(Rc + ((b0 + k) * Z + xo[k]) * V, out);
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < V; v++) pbad[v] |= par[v];
+                slot_check_dispatch<2, DMAX, V, MsgT>(dc, t_ent + b0, b0 * Z, A, Rc, r, Z, X, Xb, pbad);
             }
 #pragma unroll
             for (int v = 0; v < V; v++)
