@@ -124,6 +124,38 @@ ldpc_status ldpc_decode_batch(const ldpc_code *code, const ldpc_decode_params *p
                               uint8_t *bits_dev, int32_t *iters_dev, float *app_dev,
                               void *workspace, size_t workspace_bytes, void *stream);
 
+/* One decode request of a mixed-code launch (caller-owned device buffers, layouts as in
+ * ldpc_decode_batch). */
+typedef struct {
+    const ldpc_code *code;
+    const void *llr_dev;   /* [n_cw][N]: fp32, or int8 for the layered form with LDPC_LLR_I8 */
+    int64_t n_cw;          /* >= 0 (0: skipped)                                            */
+    uint8_t *bits_dev;     /* [n_cw][N]                                                    */
+    int32_t *iters_dev;    /* [n_cw]                                                       */
+    float *app_dev;        /* [n_cw][N] or NULL                                            */
+} ldpc_request;
+
+/* Decode several requests, possibly of different codes, in one persistent launch (Sec. III-A
+ * frame-level parallelism extended across codes).  Every codeword of every request is an item
+ * of a work queue: requests of one code form a group with its own counter, CTAs start on
+ * groups in proportion to their work and move to the group with the most work left once
+ * theirs runs dry, and a codeword's slot is refilled the moment it converges.  A codeword
+ * decodes to exactly the same result as in ldpc_decode_batch (alone or in any mix).
+ *   reqs       host array of n_req <= 128 requests over <= 16 distinct codes, all decoded
+ *              with the same params (impl must be AUTO; every code must fit the on-chip
+ *              slot decoder of the form - ldpc_decode_batch with LDPC_IMPL_STREAMING serves
+ *              larger codes).
+ *   llr_type   applies to every request.
+ *   workspace  >= ldpc_multi_workspace_size() bytes of device memory (work counters),
+ *              256-byte aligned, or NULL for a stream-ordered allocation on `stream`.
+ * The flooding forms run all requests in one launch; the layered form issues one persistent
+ * launch per request on `stream`. */
+ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldpc_decode_params *p,
+                              int32_t llr_type, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Device workspace bytes ldpc_decode_multi needs (independent of the requests). */
+ldpc_status ldpc_multi_workspace_size(size_t *bytes);
+
 /* Multi-stream host-to-host decoding (Sec. III-C: W streams, each decoding its own set
  * of frames so that copies and kernels of different sets overlap).
  *   llr_host   host, [n_cw][N] fp32 (pinned memory recommended).

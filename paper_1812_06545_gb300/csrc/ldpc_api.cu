@@ -318,7 +318,8 @@ ldpc_status ldpc_decode_batch(const ldpc_code *c, const ldpc_decode_params *p, c
     if (use_layered_slots(c, p)) {
         e = ldpc::layered_slots_decode(c->host, c->dev, *p, llr, llr_type, n_cw, bits, iters, app, ws, s);
     } else if (use_slots(c, p)) {
-        e = ldpc::slots_decode(c->host, c->dev, *p, static_cast<const float *>(llr), n_cw, bits, iters, app, ws, s);
+        const ldpc::HostReq rq = {c, llr, n_cw, bits, iters, app};
+        e = ldpc::flood_multi_decode(&rq, 1, *p, ws, s);
     } else {
         ldpc::FloodWs w;
         ldpc::flood_ws_layout(c->host, n_cw, p->msg, &w, static_cast<char *>(ws));
@@ -329,6 +330,75 @@ ldpc_status ldpc_decode_batch(const ldpc_code *c, const ldpc_decode_params *p, c
         if (e == cudaSuccess) e = e2;
     }
     return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "flooding decode launch");
+}
+
+ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldpc_decode_params *p, int32_t llr_type,
+                              void *workspace, size_t workspace_bytes, void *stream)
+{
+    if (!reqs || n_req < 0 || n_req > ldpc::MULTI_MAX_REQS)
+        return fail(LDPC_EINVAL, "need 0 <= n_req <= %d and a request array", ldpc::MULTI_MAX_REQS);
+    if (!p) return fail(LDPC_EINVAL, "params is NULL");
+    if (p->impl != LDPC_IMPL_AUTO) return fail(LDPC_ENOTSUP, "mixed-code launches use the slot decoders (impl AUTO)");
+    ldpc::HostReq hr[ldpc::MULTI_MAX_REQS];
+    const ldpc_code *seen[ldpc::MULTI_MAX_GROUPS];
+    int ncodes = 0, live = 0;
+    for (int i = 0; i < n_req; i++) {
+        const ldpc_request &q = reqs[i];
+        ldpc_status st = check_params(q.code, p, llr_type);
+        if (st != LDPC_OK) return st;
+        if (q.n_cw < 0 || q.n_cw > ((int64_t)1 << 31)) return fail(LDPC_EINVAL, "request %d: bad n_cw", i);
+        if (q.n_cw > 0 && (!q.llr_dev || !q.bits_dev || !q.iters_dev))
+            return fail(LDPC_EINVAL, "request %d: llr, bits and iters must be non-NULL", i);
+        const bool fits = p->sched == LDPC_SCHED_FLOODING ? use_slots(q.code, p) : use_layered_slots(q.code, p);
+        if (!fits) return fail(LDPC_ENOTSUP, "request %d: code too large for the slot decoders", i);
+        int g = 0;
+        while (g < ncodes && seen[g] != q.code) g++;
+        if (g == ncodes) {
+            if (ncodes == ldpc::MULTI_MAX_GROUPS)
+                return fail(LDPC_EINVAL, "more than %d distinct codes in one launch", ldpc::MULTI_MAX_GROUPS);
+            seen[ncodes++] = q.code;
+        }
+        hr[i] = {q.code, q.llr_dev, q.n_cw, q.bits_dev, q.iters_dev, q.app_dev};
+        live += q.n_cw > 0;
+    }
+    if (!live) return LDPC_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    void *ws = workspace;
+    bool own = false;
+    cudaError_t e;
+    if (ws) {
+        if (workspace_bytes < ldpc::SLOTS_WS_BYTES)
+            return fail(LDPC_ENOMEM, "workspace of %zu bytes < %zu needed", workspace_bytes, ldpc::SLOTS_WS_BYTES);
+        if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(LDPC_EINVAL, "workspace must be 256-byte aligned");
+    } else {
+        e = cudaMallocAsync(&ws, ldpc::SLOTS_WS_BYTES, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LDPC_ENOMEM, "workspace allocation failed: %s", cudaGetErrorString(e));
+        }
+        own = true;
+    }
+    if (p->sched == LDPC_SCHED_FLOODING) {
+        e = ldpc::flood_multi_decode(hr, n_req, *p, ws, s);
+    } else {
+        e = cudaSuccess;
+        for (int i = 0; i < n_req && e == cudaSuccess; i++)
+            if (hr[i].n_cw > 0)
+                e = ldpc::layered_slots_decode(hr[i].code->host, hr[i].code->dev, *p, hr[i].llr, llr_type,
+                                               hr[i].n_cw, hr[i].bits, hr[i].iters, hr[i].app, ws, s);
+    }
+    if (own) {
+        cudaError_t e2 = cudaFreeAsync(ws, s);
+        if (e == cudaSuccess) e = e2;
+    }
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "multi-request decode launch");
+}
+
+ldpc_status ldpc_multi_workspace_size(size_t *bytes)
+{
+    if (!bytes) return fail(LDPC_EINVAL, "bytes is NULL");
+    *bytes = ldpc::SLOTS_WS_BYTES;
+    return LDPC_OK;
 }
 
 // ---------------------------------------------------------------- multi-stream host path

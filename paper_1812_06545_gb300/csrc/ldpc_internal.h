@@ -66,12 +66,56 @@ cudaError_t layered_slots_decode(const CodeDev &host, const CodeDev *dev, const 
                                  int llr_type, int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out,
                                  void *counter, cudaStream_t s);
 
-// On-chip slot decoder for the flooding forms (flood_slots.cu).  counter: 8 bytes of
-// device memory, zeroed on the stream before the launch.
-constexpr size_t SLOTS_WS_BYTES = 256;
+// ---------------------------------------------------------------- slot decoders
+// Persistent decoders with per-codeword work queues (flood_slots.cu, layered_kernels.cu).
+// One launch serves up to MULTI_MAX_REQS requests over up to MULTI_MAX_GROUPS distinct
+// codes; the descriptors travel as a kernel parameter.  The work counters (8 bytes per
+// group) live in the caller's workspace and are zeroed on the stream before the launch.
+constexpr int SLOTS_MAX = 64;  // codeword slots per CTA
+constexpr int MULTI_MAX_GROUPS = 16;
+constexpr int MULTI_MAX_REQS = 128;
+constexpr size_t SLOTS_WS_BYTES = 256;  // >= 8 * MULTI_MAX_GROUPS
+
+struct ReqDev {
+    const void *llr;
+    uint8_t *bits;
+    int32_t *iters;
+    float *app;
+    int64_t n_cw;
+    int64_t item0;  // index of its first codeword in its group's work sequence
+};
+struct GroupDev {
+    const CodeDev *code;
+    int C;  // slots per CTA for this code
+    int req_begin, req_end;
+    int N, E, Z, mb, nb, nnz, dc_max;
+    int64_t n_items;
+    float cumw;  // cumulative share of the launch's work (initial CTA placement)
+};
+struct MultiDesc {
+    int n_groups;
+    GroupDev groups[MULTI_MAX_GROUPS];
+    ReqDev reqs[MULTI_MAX_REQS];
+};
+struct HostReq {
+    const ldpc_code *code;
+    const void *llr;
+    int64_t n_cw;
+    uint8_t *bits;
+    int32_t *iters;
+    float *app;
+};
+
+// Shared memory ahead of the slot arrays: per-slot bookkeeping and the code tables.
+__host__ __device__ inline size_t slots_smem_head(int tbl_ints)
+{
+    return ((size_t)SLOTS_MAX * 16 + 16 + (size_t)tbl_ints * 4 + 15) & ~(size_t)15;
+}
+
+// Flooding SPA slot decoder: supported when one codeword of the code fits a CTA.
 int slots_supported(const CodeDev &host, int msg);
-cudaError_t slots_decode(const CodeDev &host, const CodeDev *dev, const ldpc_decode_params &p, const float *llr,
-                         int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out, void *counter, cudaStream_t s);
+cudaError_t flood_multi_decode(const HostReq *reqs, int n, const ldpc_decode_params &p, void *counters,
+                               cudaStream_t s);
 
 // Record a message for ldpc_last_error() on the calling thread.
 void set_error(const char *msg);

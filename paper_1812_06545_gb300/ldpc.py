@@ -33,6 +33,11 @@ class LdpcError(RuntimeError):
         self.status = status
 
 
+class Request(C.Structure):
+    _fields_ = [("code", C.c_void_p), ("llr_dev", C.c_void_p), ("n_cw", C.c_int64), ("bits_dev", C.c_void_p),
+                ("iters_dev", C.c_void_p), ("app_dev", C.c_void_p)]
+
+
 class DecodeParams(C.Structure):
     _fields_ = [("sched", C.c_int32), ("algo", C.c_int32), ("msg", C.c_int32), ("max_iter", C.c_int32),
                 ("early_exit", C.c_int32), ("phi_clamp", C.c_float), ("nms_alpha_num", C.c_int32),
@@ -60,6 +65,8 @@ def lib():
             "ldpc_decode_batch": [vp, vp, vp, i32, i64, vp, vp, vp, vp, sz, vp],
             "ldpc_decode_host": [vp, vp, vp, i64, vp, vp, i32, i64],
             "ldpc_decode_batch_static": [vp, vp, vp, i64, vp, vp, vp, vp],
+            "ldpc_decode_multi": [vp, i32, vp, i32, vp, sz, vp],
+            "ldpc_multi_workspace_size": [vp],
             "ldpc_profile_enable": [i32],
             "ldpc_profile_read": [i32, vp, vp],
             "ldpc_profile_reset": [],
@@ -146,6 +153,22 @@ def ldpc_decode_batch(handle: int, params: DecodeParams, llr, llr_type: int, n_c
     _check(lib().ldpc_decode_batch(handle, C.byref(params), _ptr(llr), int(llr_type), int(n_cw), _ptr(bits),
                                    _ptr(iters), _ptr(app), _ptr(workspace), int(workspace_bytes), _stream(stream)),
            "ldpc_decode_batch")
+
+
+def ldpc_decode_multi(requests, params: DecodeParams, llr_type: int = LDPC_LLR_F32, workspace=None,
+                      workspace_bytes: int = 0, stream=None) -> None:
+    """requests: sequence of (code_handle, llr, n_cw, bits, iters, app_or_None)."""
+    arr = (Request * max(1, len(requests)))()
+    for i, (h, llr, n, bits, iters, app) in enumerate(requests):
+        arr[i] = Request(h, _ptr(llr), int(n), _ptr(bits), _ptr(iters), _ptr(app))
+    _check(lib().ldpc_decode_multi(arr, len(requests), C.byref(params), int(llr_type), _ptr(workspace),
+                                   int(workspace_bytes), _stream(stream)), "ldpc_decode_multi")
+
+
+def ldpc_multi_workspace_size() -> int:
+    b = C.c_size_t()
+    _check(lib().ldpc_multi_workspace_size(C.byref(b)), "ldpc_multi_workspace_size")
+    return b.value
 
 
 LDPC_STATIC_SCRATCH_BYTES = 32 << 20
