@@ -71,7 +71,7 @@ def streaming_roofline(ldpc, iters_np, steps, N, E, T, hbm_peak, peak_src):
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=150)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--streams", type=int, default=4, help="streams of the end-to-end host path")
@@ -418,6 +418,38 @@ def main():
         lms = max_over_ranks(e0.elapsed_time(e1))
         lv = world * args.steps * lw.batch * lcode.K / (lms * 1e-3) / 1e9
         lit_np = lit.cpu().numpy()
+        # mixed codes in one persistent launch: 20000 codewords over 12 codes (FP16 messages)
+        from paper_1812_06545_gb300 import inputs as I
+
+        mixed = I.mixed_batch(20000, 40 + rank)
+        mreqs, mouts, mK = [], [], 0
+        for name, c, L in mixed:
+            mb_, mZ = I.load_code(name)
+            mc = ldpc.Code(mb_, mZ)
+            x = torch.from_numpy(L).to(dev)
+            o = (torch.empty((len(L), mc.N), dtype=torch.uint8, device=dev),
+                 torch.empty((len(L),), dtype=torch.int32, device=dev))
+            mreqs.append((mc, x, len(L), o[0], o[1], None, c))
+            mK += mc.K * len(L)
+        mp = ldpc.params_for("flood_f16", max_iter=20)
+        mws = torch.empty(ldpc.ldpc_multi_workspace_size(), dtype=torch.uint8, device=dev)
+        margs = [(q[0].handle, q[1], q[2], q[3], q[4], None) for q in mreqs]
+        for _ in range(args.warmup):
+            ldpc.ldpc_decode_multi(margs, mp, ldpc.LDPC_LLR_F32, mws, mws.numel(), stream)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ldpc.ldpc_decode_multi(margs, mp, ldpc.LDPC_LLR_F32, mws, mws.numel(), stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mms = max_over_ranks(e0.elapsed_time(e1))
+        merr = sum(int((q[3].cpu().numpy() != q[6]).any(axis=1).sum()) for q in mreqs)
+        forms["mixed_f16"] = {"workload": "mixed_12codes_b20000 (Z in {27,54,81} x rate {1/2,2/3,3/4,5/6}, "
+                                          "each code at its FER~1e-2 operating point)",
+                              "value": world * args.steps * mK / (mms * 1e-3) / 1e9, "ms_per_launch": mms / args.steps,
+                              "codewords": sum(q[2] for q in mreqs), "fer": merr / sum(q[2] for q in mreqs),
+                              "api": "ldpc_decode_multi (one launch per step)"}
         forms["layered_i8"] = {"workload": LAYERED_WORKLOAD, "code": lw.code, "value": lv,
                                "ms_per_decode": lms / args.steps, "avg_iterations": float(lit_np.mean()),
                                "fer": {f"{lw.ebn0_db[0]:.2f}": float((lbits.cpu().numpy() != lframes[0][1])

@@ -124,6 +124,21 @@ ldpc_status ldpc_decode_batch(const ldpc_code *code, const ldpc_decode_params *p
                               uint8_t *bits_dev, int32_t *iters_dev, float *app_dev,
                               void *workspace, size_t workspace_bytes, void *stream);
 
+/* Choose, by timing, the schedule ldpc_decode_batch / ldpc_decode_multi use for this code
+ * and form with impl AUTO, and remember it in the code object.
+ *   Flooding forms: the on-chip slot decoder with one or two codewords per thread (where
+ *   the code fits), or the HBM-streaming kernels.  Layered form: persistent slots or the
+ *   fixed group per CTA.
+ *   llr_dev / llr_type / n_cw  a representative device sample of the workload (>= 1 codeword).
+ *   choice     receives the pick: 1 slots (1 codeword per thread), 2 slots (2 per thread),
+ *              3 streaming / fixed group (may be NULL).
+ *   ms         receives up to 3 candidate times in milliseconds, -1 for absent candidates,
+ *              in the order slots-1, slots-2, streaming (may be NULL).
+ * Synchronizes `stream` and allocates temporary device buffers; call it at set-up, before
+ * decoding with the code from other threads. */
+ldpc_status ldpc_autotune(ldpc_code *code, const ldpc_decode_params *p, const void *llr_dev, int32_t llr_type,
+                          int64_t n_cw, void *stream, int32_t *choice, float *ms);
+
 /* One decode request of a mixed-code launch (caller-owned device buffers, layouts as in
  * ldpc_decode_batch). */
 typedef struct {

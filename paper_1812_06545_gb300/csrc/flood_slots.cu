@@ -318,6 +318,8 @@ static int slots_for(const CodeDev &h, int msg, int V, int tbl_ints, size_t limi
 
 int slots_supported(const CodeDev &h, int msg) { return slots_for(h, msg, 1, tables_ints(h), 227 * 1024) > 0; }
 
+int slots_pairable(const CodeDev &h, int msg) { return slots_for(h, msg, 2, tables_ints(h), max_smem_optin()) >= 2; }
+
 // Codewords per thread: two when pairing the slots of the first code costs no slot.
 #ifndef LDPC_SLOTS_V
 #define LDPC_SLOTS_V 2
@@ -332,8 +334,7 @@ static int choose_v(const CodeDev &h, int msg, int tbl_ints, size_t limit)
 template <int DMAX, int V, typename MsgT>
 static cudaError_t launch_multi(const FloodMultiArgs &a, size_t smem, int threads, int ctas, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_flood_slots<DMAX, V, MsgT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = ensure_smem<k_flood_slots<DMAX, V, MsgT>>(smem);
     if (e != cudaSuccess) return e;
     LaunchScope ls(F_SLOTS, s);
     k_flood_slots<DMAX, V, MsgT><<<(unsigned)ctas, threads, smem, s>>>(a);
@@ -378,7 +379,10 @@ cudaError_t flood_multi_decode(const HostReq *reqs, int n, const ldpc_decode_par
         tbl = tables_ints(codes[g]->host) > tbl ? tables_ints(codes[g]->host) : tbl;
         dmax = codes[g]->host.dc_max > dmax ? codes[g]->host.dc_max : dmax;
     }
-    const int V = choose_v(codes[0]->host, p.msg, tbl, limit);
+    const int tuned = codes[0]->tuned_flood[p.msg == LDPC_MSG_F16 ? 1 : 0];
+    int V = tuned == SCHED_SLOTS_V2 ? 2 : tuned == SCHED_SLOTS_V1 ? 1 : choose_v(codes[0]->host, p.msg, tbl, limit);
+    for (int g = 0; g < ng && V == 2; g++)
+        if (slots_for(codes[g]->host, p.msg, 2, tbl, limit) < 2) V = 1;
     size_t smem = 0;
     int threads = 32;
     double wsum = 0.0;

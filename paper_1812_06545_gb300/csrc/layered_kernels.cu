@@ -348,7 +348,7 @@ template <int DMAX>
 static cudaError_t launch_layered(const CodeDev &h, const CodeDev *d, const LayeredArgs &a, cudaStream_t s)
 {
     const size_t sm = layered_smem(h, a.C);
-    cudaError_t e = cudaFuncSetAttribute(k_layered_nms<DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = ensure_smem<k_layered_nms<DMAX>>(sm);
     if (e != cudaSuccess) return e;
     const int threads = ((a.C * h.Z + 31) / 32) * 32;
     const unsigned blocks = (unsigned)((a.n_cw + a.C - 1) / a.C);
@@ -375,7 +375,7 @@ template <int DMAX>
 static cudaError_t launch_lslots(const CodeDev &h, const CodeDev *d, const LayeredSlotArgs &a, cudaStream_t s)
 {
     const size_t sm = lslots_smem(h, a.C);
-    cudaError_t e = cudaFuncSetAttribute(k_layered_slots<DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = ensure_smem<k_layered_slots<DMAX>>(sm);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);

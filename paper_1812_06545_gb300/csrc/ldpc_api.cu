@@ -137,6 +137,9 @@ ldpc_status ldpc_code_create(const int32_t *base, int32_t mb, int32_t nb, int32_
     ldpc_code *c = new (std::nothrow) ldpc_code;
     if (!c) return fail(LDPC_ENOMEM, "host allocation failed");
     memset(&c->host, 0, sizeof c->host);
+    c->dev = nullptr;
+    c->tuned_flood[0] = c->tuned_flood[1] = SCHED_UNTUNED;
+    c->tuned_layered = SCHED_UNTUNED;
     CodeDev &h = c->host;
     h.mb = mb;
     h.nb = nb;
@@ -256,14 +259,16 @@ static ldpc_status check_params(const ldpc_code *c, const ldpc_decode_params *p,
 // a CTA's shared memory; LDPC_IMPL_STREAMING and the plain comparator use the HBM layout.
 static bool use_slots(const ldpc_code *c, const ldpc_decode_params *p)
 {
-    return p->sched == LDPC_SCHED_FLOODING && p->impl == LDPC_IMPL_AUTO && ldpc::slots_supported(c->host, p->msg);
+    return p->sched == LDPC_SCHED_FLOODING && p->impl == LDPC_IMPL_AUTO && ldpc::slots_supported(c->host, p->msg) &&
+           c->tuned_flood[p->msg == LDPC_MSG_F16 ? 1 : 0] != SCHED_STREAMING;
 }
 
 // The layered min-sum runs as persistent slots (work counter in the workspace) unless
 // LDPC_IMPL_STREAMING asks for the one-CTA-per-group kernel, which needs no workspace.
 static bool use_layered_slots(const ldpc_code *c, const ldpc_decode_params *p)
 {
-    return p->sched == LDPC_SCHED_LAYERED && p->impl == LDPC_IMPL_AUTO && ldpc::layered_slots_per_cta(c->host) > 0;
+    return p->sched == LDPC_SCHED_LAYERED && p->impl == LDPC_IMPL_AUTO && ldpc::layered_slots_per_cta(c->host) > 0 &&
+           c->tuned_layered != SCHED_STREAMING;
 }
 
 static size_t ws_bytes(const ldpc_code *c, const ldpc_decode_params *p, int64_t n_cw)
@@ -392,6 +397,75 @@ ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldp
         if (e == cudaSuccess) e = e2;
     }
     return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "multi-request decode launch");
+}
+
+ldpc_status ldpc_autotune(ldpc_code *c, const ldpc_decode_params *p, const void *llr, int32_t llr_type, int64_t n_cw,
+                          void *stream, int32_t *choice, float *ms)
+{
+    if (p && p->impl != LDPC_IMPL_AUTO) return fail(LDPC_EINVAL, "autotuning chooses the AUTO schedule (impl AUTO)");
+    ldpc_status st = check_params(c, p, llr_type);
+    if (st != LDPC_OK) return st;
+    if (n_cw < 1 || !llr) return fail(LDPC_EINVAL, "autotuning needs a non-empty sample of LLRs");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int *slot = p->sched == LDPC_SCHED_FLOODING ? &c->tuned_flood[p->msg == LDPC_MSG_F16 ? 1 : 0] : &c->tuned_layered;
+    int cand[3], nc = 0;
+    if (p->sched == LDPC_SCHED_FLOODING) {
+        if (ldpc::slots_supported(c->host, p->msg)) {
+            cand[nc++] = SCHED_SLOTS_V1;
+            if (ldpc::slots_pairable(c->host, p->msg)) cand[nc++] = SCHED_SLOTS_V2;
+        }
+    } else if (ldpc::layered_slots_per_cta(c->host) > 0) {
+        cand[nc++] = SCHED_SLOTS_V1;
+    }
+    cand[nc++] = SCHED_STREAMING;
+    uint8_t *bits = nullptr;
+    int32_t *it = nullptr;
+    void *ws = nullptr;
+    size_t wsb = 0;
+    {
+        const int saved = *slot;
+        *slot = SCHED_STREAMING;
+        wsb = ws_bytes(c, p, n_cw);
+        *slot = saved;
+        if (wsb < ldpc::SLOTS_WS_BYTES) wsb = ldpc::SLOTS_WS_BYTES;
+    }
+    cudaError_t e = cudaMalloc(&bits, (size_t)n_cw * c->host.N);
+    if (e == cudaSuccess) e = cudaMalloc(&it, (size_t)n_cw * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&ws, wsb);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    int pick = SCHED_UNTUNED;
+    for (int i = 0; i < nc && e == cudaSuccess; i++) {
+        *slot = cand[i];
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {
+            if (rep) e = cudaEventRecord(e0, s);
+            st = ldpc_decode_batch(c, p, llr, llr_type, n_cw, bits, it, nullptr, ws, wsb, stream);
+            if (st != LDPC_OK) e = cudaErrorUnknown;
+            if (rep && e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (rep && e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (rep && e == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess && t < tmin) tmin = t;
+        }
+        if (ms) ms[i] = tmin;
+        if (tmin < best) {
+            best = tmin;
+            pick = cand[i];
+        }
+    }
+    if (ms)
+        for (int i = nc; i < 3; i++) ms[i] = -1.0f;
+    *slot = e == cudaSuccess ? pick : SCHED_UNTUNED;
+    if (choice) *choice = *slot;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(bits);
+    cudaFree(it);
+    cudaFree(ws);
+    if (st != LDPC_OK) return st;
+    return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "autotune");
 }
 
 ldpc_status ldpc_multi_workspace_size(size_t *bytes)

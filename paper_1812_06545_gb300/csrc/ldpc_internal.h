@@ -114,6 +114,7 @@ __host__ __device__ inline size_t slots_smem_head(int tbl_ints)
 
 // Flooding SPA slot decoder: supported when one codeword of the code fits a CTA.
 int slots_supported(const CodeDev &host, int msg);
+int slots_pairable(const CodeDev &host, int msg);
 cudaError_t flood_multi_decode(const HostReq *reqs, int n, const ldpc_decode_params &p, void *counters,
                                cudaStream_t s);
 
@@ -122,8 +123,31 @@ void set_error(const char *msg);
 
 }  // namespace ldpc
 
+// Schedule choices stored by ldpc_autotune (0: not tuned, the built-in heuristic decides).
+enum Schedule { SCHED_UNTUNED = 0, SCHED_SLOTS_V1 = 1, SCHED_SLOTS_V2 = 2, SCHED_STREAMING = 3 };
+
 struct ldpc_code {
     ldpc::CodeDev host;
     ldpc::CodeDev *dev;
     int device;
+    int tuned_flood[2];  // per message type (F32, F16)
+    int tuned_layered;
 };
+
+namespace ldpc {
+// Raise a kernel's dynamic shared-memory limit once per device and size.  The attribute is
+// host-side state; setting it only when it grows keeps repeated launches (and launches
+// inside a stream capture, after the first eager one) free of the call.
+template <auto Kernel>
+inline cudaError_t ensure_smem(size_t bytes)
+{
+    static int set_bytes[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if ((size_t)__atomic_load_n(&set_bytes[dev], __ATOMIC_RELAXED) >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) __atomic_store_n(&set_bytes[dev], (int)bytes, __ATOMIC_RELAXED);
+    return e;
+}
+}  // namespace ldpc

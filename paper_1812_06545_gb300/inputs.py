@@ -240,6 +240,31 @@ WORKLOADS = {
 }
 
 
+MIXED_FAMILY = sorted(n for n in CODE_SPECS if n.endswith(tuple(f"_s{s}" for s in range(40, 52))))
+
+
+def operating_points() -> dict:
+    """Eb/N0 per mixed-family code at which the FP64 oracle's frame error rate is about
+    1e-2 (committed data; see its 'written_by' field)."""
+    import json
+
+    with open(os.path.join(CODES_DIR, "operating_points.json")) as f:
+        return {k: v["ebn0_db"] for k, v in json.load(f)["points"].items()}
+
+
+def mixed_batch(n_total: int = 20000, seed: int = 40):
+    """The mixed-code workload: n_total codewords, each drawn uniformly from the 12 codes
+    Z in {27, 54, 81} x rate {1/2, 2/3, 3/4, 5/6} (seeded multinomial), every code at its
+    operating point.  Returns [(code name, c uint8 [n, N], L fp32 [n, N])] in family order."""
+    ops = operating_points()
+    counts = np.random.Generator(np.random.PCG64(seed)).multinomial(n_total, [1 / len(MIXED_FAMILY)] * len(MIXED_FAMILY))
+    out = []
+    for i, (name, n) in enumerate(zip(MIXED_FAMILY, counts)):
+        _, _, c, L = make_frames(name, int(n), ops[name], seed * 100 + i, seed * 100 + 50 + i)
+        out.append((name, c, L))
+    return out
+
+
 def make_frames(code: str, n: int, ebn0_db: float, info_seed: int, noise_seed: int):
     """Encode n random-info codewords of ``code`` and pass them through BPSK/AWGN.
 

@@ -67,6 +67,7 @@ def lib():
             "ldpc_decode_batch_static": [vp, vp, vp, i64, vp, vp, vp, vp],
             "ldpc_decode_multi": [vp, i32, vp, i32, vp, sz, vp],
             "ldpc_multi_workspace_size": [vp],
+            "ldpc_autotune": [vp, vp, vp, i32, i64, vp, vp, vp],
             "ldpc_profile_enable": [i32],
             "ldpc_profile_read": [i32, vp, vp],
             "ldpc_profile_reset": [],
@@ -163,6 +164,15 @@ def ldpc_decode_multi(requests, params: DecodeParams, llr_type: int = LDPC_LLR_F
         arr[i] = Request(h, _ptr(llr), int(n), _ptr(bits), _ptr(iters), _ptr(app))
     _check(lib().ldpc_decode_multi(arr, len(requests), C.byref(params), int(llr_type), _ptr(workspace),
                                    int(workspace_bytes), _stream(stream)), "ldpc_decode_multi")
+
+
+def ldpc_autotune(handle: int, params: DecodeParams, llr, llr_type: int, n_cw: int, stream=None):
+    """Time the candidate schedules on a device sample; returns (choice, [ms per candidate])."""
+    choice = C.c_int32()
+    ms = (C.c_float * 3)()
+    _check(lib().ldpc_autotune(handle, C.byref(params), _ptr(llr), int(llr_type), int(n_cw), _stream(stream),
+                               C.byref(choice), ms), "ldpc_autotune")
+    return choice.value, list(ms)
 
 
 def ldpc_multi_workspace_size() -> int:
