@@ -184,6 +184,76 @@ ldpc_status ldpc_decode_host(const ldpc_code *code, const ldpc_decode_params *p,
                              int64_t n_cw, uint8_t *bits_host, int32_t *iters_host, int32_t n_streams,
                              int64_t chunk_cw);
 
+/* ------------------------------------------------------------------ serving loop
+ *
+ * A session decodes requests submitted from any host thread, continuously batching them
+ * onto the GPU (Sec. III-C: several sets of frames in flight on their own streams).  A
+ * dispatcher thread keeps up to max_inflight launches going; whenever one finishes (or a
+ * request arrives while a slot is free) it admits the longest prefix of the FIFO queue that
+ * shares one parameter set, spans at most 16 codes, holds at most max_batch requests and
+ * fits the remaining device-memory budget, and issues it on its own stream as: host-to-device
+ * copies, one persistent multi-request decode (the codewords of every admitted request are
+ * items of one work queue; codes the on-chip decoders cannot hold are decoded alone), and
+ * device-to-host copies.  A request's result does not depend on what it was batched with. */
+typedef struct ldpc_session ldpc_session;
+
+typedef struct {
+    size_t hbm_budget_bytes;  /* device memory for request buffers, reserved at creation (>= 1 MiB) */
+    int32_t max_inflight;     /* concurrent launches / streams, 1..16 (default 4)                    */
+    int32_t max_batch;        /* requests per launch, 1..128 (default 128)                           */
+    int32_t start_paused;     /* 1: admit nothing until ldpc_session_pause(s, 0)                     */
+    int32_t fail_alloc_after; /* fault injection: the n-th buffer allocation fails (0: off); that     */
+                              /* request finishes with LDPC_ENOMEM and the session carries on         */
+    int32_t reserved[4];      /* zero                                                                */
+} ldpc_session_config;
+
+typedef struct {
+    int64_t submitted, completed, failed, cancelled, queued, launches;
+    size_t budget_bytes, bytes_in_use, peak_bytes; /* request-buffer memory of the arena */
+} ldpc_session_stats;
+
+/* Request states reported by ldpc_session_poll. */
+enum { LDPC_REQ_QUEUED = 0, LDPC_REQ_RUNNING = 1, LDPC_REQ_DONE = 2, LDPC_REQ_FAILED = 3, LDPC_REQ_CANCELLED = 4 };
+
+ldpc_status ldpc_session_default_config(ldpc_session_config *cfg);
+
+/* Create a session on the current device: reserves hbm_budget_bytes of device memory and
+ * starts the dispatcher thread. */
+ldpc_status ldpc_session_create(const ldpc_session_config *cfg, ldpc_session **out);
+
+/* Queue n_cw >= 1 codewords of `code` for decoding with params *p.
+ *   llr_host   host [n_cw][N] fp32 LLRs; bits_host host [n_cw][N]; iters_host [n_cw] or NULL.
+ *              Caller-owned; they must stay valid until the request is reported finished
+ *              (pinned memory lets the copies overlap the decoding of other requests).
+ *   req_id     receives the request's id.
+ * Returns LDPC_ENOMEM if the request alone exceeds the memory budget, LDPC_EINVAL /
+ * LDPC_ENOTSUP for bad arguments; nothing is queued then. */
+ldpc_status ldpc_session_submit(ldpc_session *s, const ldpc_code *code, const ldpc_decode_params *p,
+                                const float *llr_host, int64_t n_cw, uint8_t *bits_host, int32_t *iters_host,
+                                uint64_t *req_id);
+
+/* Non-blocking status: *state receives LDPC_REQ_*.  Once a finished state is reported the
+ * request's record is released (its id becomes unknown) and the return value is the
+ * request's own status (LDPC_OK, or e.g. LDPC_ENOMEM / LDPC_ECUDA for a failed request);
+ * *latency_s then receives the time from submission to completion. */
+ldpc_status ldpc_session_poll(ldpc_session *s, uint64_t req_id, int32_t *state, double *latency_s);
+
+/* Block until the request finishes (then as ldpc_session_poll) or timeout_s elapses
+ * (LDPC_ETIMEDOUT, record kept). */
+ldpc_status ldpc_session_wait(ldpc_session *s, uint64_t req_id, double timeout_s, double *latency_s);
+
+/* Cancel a queued request (LDPC_EBUSY once it is on the GPU; finished ones are left alone). */
+ldpc_status ldpc_session_cancel(ldpc_session *s, uint64_t req_id);
+
+/* Stop (paused = 1) or restart (0) admitting queued requests; launches in flight finish. */
+ldpc_status ldpc_session_pause(ldpc_session *s, int32_t paused);
+
+ldpc_status ldpc_session_stats_get(ldpc_session *s, ldpc_session_stats *out);
+
+/* Stop the dispatcher, wait for launches in flight and free the session (queued requests
+ * are dropped). */
+void ldpc_session_destroy(ldpc_session *s);
+
 /* Release the device buffers and streams ldpc_decode_host keeps for the calling thread. */
 void ldpc_release_host_buffers(void);
 

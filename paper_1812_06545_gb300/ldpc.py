@@ -38,6 +38,20 @@ class Request(C.Structure):
                 ("iters_dev", C.c_void_p), ("app_dev", C.c_void_p)]
 
 
+class SessionConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_inflight", C.c_int32), ("max_batch", C.c_int32),
+                ("start_paused", C.c_int32), ("fail_alloc_after", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class SessionStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("cancelled", C.c_int64),
+                ("queued", C.c_int64), ("launches", C.c_int64), ("budget_bytes", C.c_size_t),
+                ("bytes_in_use", C.c_size_t), ("peak_bytes", C.c_size_t)]
+
+
+LDPC_REQ_QUEUED, LDPC_REQ_RUNNING, LDPC_REQ_DONE, LDPC_REQ_FAILED, LDPC_REQ_CANCELLED = 0, 1, 2, 3, 4
+
+
 class DecodeParams(C.Structure):
     _fields_ = [("sched", C.c_int32), ("algo", C.c_int32), ("msg", C.c_int32), ("max_iter", C.c_int32),
                 ("early_exit", C.c_int32), ("phi_clamp", C.c_float), ("nms_alpha_num", C.c_int32),
@@ -68,6 +82,14 @@ def lib():
             "ldpc_decode_multi": [vp, i32, vp, i32, vp, sz, vp],
             "ldpc_multi_workspace_size": [vp],
             "ldpc_autotune": [vp, vp, vp, i32, i64, vp, vp, vp],
+            "ldpc_session_default_config": [vp],
+            "ldpc_session_create": [vp, vp],
+            "ldpc_session_submit": [vp, vp, vp, vp, i64, vp, vp, vp],
+            "ldpc_session_poll": [vp, C.c_uint64, vp, vp],
+            "ldpc_session_wait": [vp, C.c_uint64, C.c_double, vp],
+            "ldpc_session_cancel": [vp, C.c_uint64],
+            "ldpc_session_pause": [vp, i32],
+            "ldpc_session_stats_get": [vp, vp],
             "ldpc_profile_enable": [i32],
             "ldpc_profile_read": [i32, vp, vp],
             "ldpc_profile_reset": [],
@@ -76,6 +98,8 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = C.c_int
+        L.ldpc_session_destroy.argtypes = [vp]
+        L.ldpc_session_destroy.restype = None
         L.ldpc_code_destroy.argtypes = [vp]
         L.ldpc_code_destroy.restype = None
         L.ldpc_release_host_buffers.argtypes = []
@@ -173,6 +197,62 @@ def ldpc_autotune(handle: int, params: DecodeParams, llr, llr_type: int, n_cw: i
     _check(lib().ldpc_autotune(handle, C.byref(params), _ptr(llr), int(llr_type), int(n_cw), _stream(stream),
                                C.byref(choice), ms), "ldpc_autotune")
     return choice.value, list(ms)
+
+
+def ldpc_session_default_config(**overrides) -> SessionConfig:
+    c = SessionConfig()
+    _check(lib().ldpc_session_default_config(C.byref(c)), "ldpc_session_default_config")
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def ldpc_session_create(cfg: SessionConfig) -> int:
+    h = C.c_void_p()
+    _check(lib().ldpc_session_create(C.byref(cfg), C.byref(h)), "ldpc_session_create")
+    return h.value
+
+
+def ldpc_session_submit(sess: int, code_handle: int, params: DecodeParams, llr_host, n_cw: int, bits_host,
+                        iters_host=None) -> int:
+    rid = C.c_uint64()
+    _check(lib().ldpc_session_submit(sess, code_handle, C.byref(params), _ptr(llr_host), int(n_cw), _ptr(bits_host),
+                                     _ptr(iters_host), C.byref(rid)), "ldpc_session_submit")
+    return rid.value
+
+
+def ldpc_session_poll(sess: int, rid: int):
+    """-> (state, status, latency_s); status/latency only meaningful for finished states."""
+    st, lat = C.c_int32(), C.c_double()
+    rc = lib().ldpc_session_poll(sess, rid, C.byref(st), C.byref(lat))
+    if st.value < LDPC_REQ_DONE and rc != LDPC_OK:
+        _check(rc, "ldpc_session_poll")
+    return st.value, rc, lat.value
+
+
+def ldpc_session_wait(sess: int, rid: int, timeout_s: float) -> tuple[int, float]:
+    """-> (status, latency_s); status LDPC_ETIMEDOUT if not finished in time."""
+    lat = C.c_double()
+    rc = lib().ldpc_session_wait(sess, rid, float(timeout_s), C.byref(lat))
+    return rc, lat.value
+
+
+def ldpc_session_cancel(sess: int, rid: int) -> int:
+    return lib().ldpc_session_cancel(sess, rid)
+
+
+def ldpc_session_pause(sess: int, paused: bool) -> None:
+    _check(lib().ldpc_session_pause(sess, 1 if paused else 0), "ldpc_session_pause")
+
+
+def ldpc_session_stats_get(sess: int) -> SessionStats:
+    st = SessionStats()
+    _check(lib().ldpc_session_stats_get(sess, C.byref(st)), "ldpc_session_stats_get")
+    return st
+
+
+def ldpc_session_destroy(sess: int) -> None:
+    lib().ldpc_session_destroy(sess)
 
 
 def ldpc_multi_workspace_size() -> int:
