@@ -78,6 +78,8 @@ def parse_args():
     ap.add_argument("--no-forms", action="store_true", help="time only the headline form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--serve-seconds", type=float, default=1.5, help="arrival window per offered rate")
     return ap.parse_args()
 
 
@@ -178,6 +180,101 @@ def oracle_sample_rate(frames, code_name: str, max_iter: int, budget_s: float, t
     rate = n * len(frames) * oc.K / dt
     return rate, f"first {n} codewords of each of the {len(frames)} Eb/N0 batches ({n * len(frames)} codewords)", \
         cores, errs, n * len(frames)
+
+
+# ------------------------------------------------------------------ serving loop
+
+def run_serving(ldpc, dev, window_s: float):
+    """Poisson arrivals of requests of 1..512 codewords, each of one code drawn uniformly from
+    the 12-code family plus the N = 26112 code, half FP16 sum-product and half int8 layered
+    min-sum, into one ldpc_session.  A closed-loop burst first measures the session's
+    capacity; the offered rate is then swept as fractions of it.  Latency is the session's
+    own submission-to-completion stamp."""
+    import torch
+
+    from paper_1812_06545_gb300 import inputs as I
+
+    rng = np.random.default_rng(5)
+    names = I.MIXED_FAMILY + ["qc34x68_z384_s5"]
+    ops = I.operating_points()
+    pool = []
+    for k, name in enumerate(names):
+        B, Z = I.load_code(name)
+        code = ldpc.Code(B, Z)
+        n = 512
+        _, _, c, L = I.make_frames(name, n, ops.get(name, 2.0), 500 + k, 600 + k)
+        pool.append((code, torch.from_numpy(L).pin_memory(), torch.empty((n, code.N), dtype=torch.uint8).pin_memory(),
+                     torch.empty((n,), dtype=torch.int32).pin_memory()))
+    forms = {"flood_f16": ldpc.params_for("flood_f16", max_iter=20),
+             "layered_i8": ldpc.params_for("layered_i8", max_iter=10)}
+    cfg = ldpc.ldpc_session_default_config(hbm_budget_bytes=16 << 30, max_inflight=4)
+    sess = ldpc.ldpc_session_create(cfg)
+
+    def draw():
+        k = int(rng.integers(len(pool)))
+        n = int(rng.integers(1, 513))
+        form = "flood_f16" if rng.random() < 0.5 else "layered_i8"
+        return k, n, form
+
+    def submit(k, n, form):
+        code, L, bits, it = pool[k]
+        o = int(rng.integers(0, 513 - n))
+        return ldpc.ldpc_session_submit(sess, code.handle, forms[form], L[o:o + n], n, bits[o:o + n],
+                                        it[o:o + n]), code.K * n
+
+    def collect(ids):
+        lat, bits_done = [], 0
+        for rid, kb in ids:
+            st, t = ldpc.ldpc_session_wait(sess, rid, 120.0)
+            if st == 0:
+                lat.append(t)
+                bits_done += kb
+        return lat, bits_done
+
+    try:
+        for _ in range(2):  # warm-up (tables, attributes, pinned-memory paths)
+            collect([submit(*draw()) for _ in range(32)])
+        burst = [draw() for _ in range(1500)]
+        t0 = time.perf_counter()
+        ids = [submit(*d) for d in burst]
+        lat, kb = collect(ids)
+        t_cap = time.perf_counter() - t0
+        cap_rps = len(burst) / t_cap
+        cap_gbps = kb / t_cap / 1e9
+        out = {"workload": "requests of 1-512 codewords, code uniform over 12 family codes + N=26112 code, "
+                           "half FP16 SPA / half int8 layered NMS, Poisson arrivals",
+               "session": {"hbm_budget_bytes": cfg.hbm_budget_bytes, "max_inflight": cfg.max_inflight,
+                           "max_batch": cfg.max_batch},
+               "capacity": {"requests_per_s": cap_rps, "info_gbps": cap_gbps, "burst_requests": len(burst)},
+               "sweep": []}
+        for frac in (0.25, 0.5, 0.75, 0.9, 1.0, 1.2):
+            rate = frac * cap_rps
+            ids = []
+            t0 = time.perf_counter()
+            t_next = t0
+            while True:
+                now = time.perf_counter()
+                if now - t0 >= window_s:
+                    break
+                if now < t_next:
+                    continue
+                ids.append(submit(*draw()))
+                t_next += rng.exponential(1.0 / rate)
+            lat, kb = collect(ids)
+            t_all = time.perf_counter() - t0
+            lat_ms = np.array(lat) * 1e3
+            out["sweep"].append({"offered_fraction": frac, "offered_rps": rate, "requests": len(ids),
+                                 "achieved_info_gbps": kb / t_all / 1e9,
+                                 "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99))})
+        sat = [x for x in out["sweep"] if x["offered_fraction"] == 1.0][0]
+        out["at_saturation"] = {"achieved_info_gbps": sat["achieved_info_gbps"], "p50_ms": sat["p50_ms"],
+                                "p99_ms": sat["p99_ms"]}
+        st = ldpc.ldpc_session_stats_get(sess)
+        out["stats"] = {"launches": st.launches, "completed": st.completed, "failed": st.failed,
+                        "peak_bytes": st.peak_bytes}
+        return out
+    finally:
+        ldpc.ldpc_session_destroy(sess)
 
 
 # ------------------------------------------------------------------ reference arm (the oracle)
@@ -482,6 +579,10 @@ def main():
     e2e["matches_device_path"] = bool(ok)
     line["e2e"] = e2e
     ldpc.ldpc_release_host_buffers()
+
+    # ---------------- serving loop: Poisson arrivals of mixed requests (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_serving:
+        line["serving"] = run_serving(ldpc, dev, args.serve_seconds)
 
     # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
