@@ -189,9 +189,10 @@ ldpc_status ldpc_decode_host(const ldpc_code *code, const ldpc_decode_params *p,
  * A session decodes requests submitted from any host thread, continuously batching them
  * onto the GPU (Sec. III-C: several sets of frames in flight on their own streams).  A
  * dispatcher thread keeps up to max_inflight launches going; whenever one finishes (or a
- * request arrives while a slot is free) it admits the longest prefix of the FIFO queue that
- * shares one parameter set, spans at most 16 codes, holds at most max_batch requests and
- * fits the remaining device-memory budget, and issues it on its own stream as: host-to-device
+ * request arrives while a slot is free) it admits the head of the FIFO queue together with
+ * the queued requests that share its parameter set (at most max_batch requests over at most
+ * 16 codes, as the remaining device-memory budget allows; no request overtakes one waiting
+ * for memory), and issues them on their own stream as: host-to-device
  * copies, one persistent multi-request decode (the codewords of every admitted request are
  * items of one work queue; codes the on-chip decoders cannot hold are decoded alone), and
  * device-to-host copies.  A request's result does not depend on what it was batched with. */

@@ -3,9 +3,9 @@
 // thread keeps up to max_inflight launches going on their own streams).
 //
 // Continuous batching: submitted requests wait in a FIFO queue.  Whenever a stream slot is
-// free, the dispatcher admits the longest prefix of the queue that shares one parameter set,
-// fits the remaining device-memory budget and spans at most MULTI_MAX_GROUPS codes, and
-// issues it as one launch on that stream: copies in, one persistent multi-request decode
+// free, the dispatcher admits the head of the queue together with the queued requests that
+// share its parameter set (up to max_batch requests over at most MULTI_MAX_GROUPS codes, as
+// memory allows), and issues them as one launch on that stream: copies in, one persistent multi-request decode
 // (every codeword an item of the work queue), copies out, and a host callback that stamps
 // the requests' latencies and returns their memory.  Requests that arrive while others are
 // on the GPU are therefore admitted as soon as memory and a slot free up, and their work
@@ -30,6 +30,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr size_t kAlign = 256;
+constexpr size_t kLookahead = 1024;  // queued requests the dispatcher scans for a batch
 inline size_t al(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct Block {
@@ -247,22 +248,35 @@ void worker_loop(ldpc_session *s)
         std::vector<SessReq *> batch;
         std::vector<uint64_t> ids;
         if (free_slot && !s->paused) {
+            // The head of the queue always goes first; batchable requests further back with
+            // the head's parameters join it (within a look-ahead window), so a mix of forms
+            // still fills launches.  The first request that does not fit in memory stops the
+            // scan: nothing overtakes a request waiting for memory.
             const ldpc_code *codes[ldpc::MULTI_MAX_GROUPS];
             int ncodes = 0;
-            while (!s->queue.empty() && (int)batch.size() < s->cfg.max_batch) {
-                const uint64_t id = s->queue.front();
+            size_t scanned = 0;
+            for (auto qi = s->queue.begin(); qi != s->queue.end() && (int)batch.size() < s->cfg.max_batch &&
+                                             scanned < kLookahead;
+                 scanned++) {
+                const uint64_t id = *qi;
                 SessReq &r = s->reqs[id];
-                if (!batch.empty() && (!batch[0]->batchable || !r.batchable || !same_params(r.p, batch[0]->p))) break;
+                if (!batch.empty() && (!batch[0]->batchable || !r.batchable || !same_params(r.p, batch[0]->p))) {
+                    ++qi;
+                    continue;
+                }
                 int g = 0;
                 while (g < ncodes && codes[g] != r.code) g++;
-                if (g == ncodes && ncodes == ldpc::MULTI_MAX_GROUPS) break;
+                if (g == ncodes && ncodes == ldpc::MULTI_MAX_GROUPS) {
+                    ++qi;
+                    continue;
+                }
                 bool ok = true;
                 if (s->cfg.fail_alloc_after > 0 && ++s->allocs == s->cfg.fail_alloc_after) {
                     ok = false;  // injected allocation failure: this request fails, the rest go on
                 } else if (!s->arena.alloc(r.bytes, &r.blk)) {
                     break;  // wait for memory to come back
                 }
-                s->queue.pop_front();
+                qi = s->queue.erase(qi);
                 if (!ok) {
                     r.state = RS_FAILED;
                     r.status = LDPC_ENOMEM;
