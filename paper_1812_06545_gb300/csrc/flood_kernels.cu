@@ -24,7 +24,7 @@ namespace ldpc {
 // ------------------------------------------------------------------ phi
 
 // phi(x) = -ln tanh(x/2) = ln((1 + t)/(1 - t)) with t = e^-x, on the hardware
-// approximations ex2 / lg2 / rcp (PTX *.approx.ftz.f32).  The check rule needs phi twice
+// approximations ex2 / lg2 (PTX *.approx.ftz.f32).  The check rule needs phi twice
 // per edge with different accuracy demands, so there are two evaluations:
 //
 //   psi_in(x)  = phi(x) / ln 2 for the incoming |Q| (base-2 units).  Small values (large x)
@@ -52,21 +52,16 @@ __device__ __forceinline__ float lg2_approx(float x)
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
+// ln((1 + t)/(1 - t)) = lg2(1 + t) - lg2(1 - t): two independent logarithms of opposite
+// sign (no cancellation), a shorter dependency chain than a reciprocal and one logarithm.
 __device__ __forceinline__ float psi_in(float x)
 {
     const float t = ex2_approx(-x * kLog2e);
     const float big = t * fmaf(t * t, (2.0f / 3.0f) * kLog2e, 2.0f * kLog2e);
-    const float mid = lg2_approx((1.0f + t) * rcp_approx(1.0f - t));
+    const float mid = lg2_approx(1.0f + t) - lg2_approx(1.0f - t);
     return x > 3.0f ? big : mid;
 }
 
@@ -75,7 +70,7 @@ __device__ __forceinline__ float phi_out(float s2)
     const float t = ex2_approx(-s2);
     const float S = s2 * kLn2;
     const float den = S < 0.0625f ? S * fmaf(S, fmaf(S, 1.0f / 6.0f, -0.5f), 1.0f) : 1.0f - t;
-    return lg2_approx((1.0f + t) * rcp_approx(den)) * kLn2;
+    return (lg2_approx(1.0f + t) - lg2_approx(den)) * kLn2;
 }
 
 // The plain comparator's phi: the definition log1p(2 / expm1(x)) with the library's

@@ -20,20 +20,17 @@ __device__ __forceinline__ float s_lg2(float x)
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-__device__ __forceinline__ float s_rcp(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 constexpr float kSLog2e = 1.4426950408889634f;
 constexpr float kSLn2 = 0.6931471805599453f;
 
+// ln((1 + t)/(1 - t)) is evaluated as lg2(1 + t) - lg2(1 - t): the two logarithms are
+// independent (a shorter dependency chain than a reciprocal followed by one logarithm) and
+// have opposite signs, so their difference does not cancel.
 __device__ __forceinline__ float s_psi_in(float x)
 {
     const float t = s_ex2(-x * kSLog2e);
     const float big = t * fmaf(t * t, (2.0f / 3.0f) * kSLog2e, 2.0f * kSLog2e);
-    const float mid = s_lg2((1.0f + t) * s_rcp(1.0f - t));
+    const float mid = s_lg2(1.0f + t) - s_lg2(1.0f - t);
     return x > 3.0f ? big : mid;
 }
 
@@ -42,7 +39,7 @@ __device__ __forceinline__ float s_phi_out(float s2)
     const float t = s_ex2(-s2);
     const float S = s2 * kSLn2;
     const float den = S < 0.0625f ? S * fmaf(S, fmaf(S, 1.0f / 6.0f, -0.5f), 1.0f) : 1.0f - t;
-    return s_lg2((1.0f + t) * s_rcp(den)) * kSLn2;
+    return (s_lg2(1.0f + t) - s_lg2(den)) * kSLn2;
 }
 
 // V consecutive slots share each shared-memory element group: APP and R are laid out
@@ -153,20 +150,114 @@ __device__ __forceinline__ void slot_check(int dc, const int32_t *__restrict__ e
     for (int v = 0; v < V; v++) pbad[v] |= par[v];
 }
 
+// The same check for two codewords held as float2: the FP32 multiplies, adds and FMAs of
+// both phi evaluations and of the prefix / suffix sums issue as packed pairs (FMUL2, FADD2,
+// FFMA2 on sm_100+); the special functions, min/max, selects and sign-bit logic stay scalar.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ float2 psi_in2(float2 x)
+{
+    const float2 arg = __fmul2_rn(x, f2(-kSLog2e, -kSLog2e));
+    const float2 t = f2(s_ex2(arg.x), s_ex2(arg.y));
+    const float2 big = __fmul2_rn(t, __ffma2_rn(__fmul2_rn(t, t), f2((2.0f / 3.0f) * kSLog2e, (2.0f / 3.0f) * kSLog2e),
+                                                f2(2.0f * kSLog2e, 2.0f * kSLog2e)));
+    const float2 num = __fadd2_rn(t, f2(1.0f, 1.0f));
+    const float2 den = __ffma2_rn(t, f2(-1.0f, -1.0f), f2(1.0f, 1.0f));
+    const float2 mid = __fadd2_rn(f2(s_lg2(num.x), s_lg2(num.y)), f2(-s_lg2(den.x), -s_lg2(den.y)));
+    return f2(x.x > 3.0f ? big.x : mid.x, x.y > 3.0f ? big.y : mid.y);
+}
+
+__device__ __forceinline__ float2 phi_out2(float2 s2)
+{
+    const float2 t = f2(s_ex2(-s2.x), s_ex2(-s2.y));
+    const float2 S = __fmul2_rn(s2, f2(kSLn2, kSLn2));
+    const float2 poly = __fmul2_rn(S, __ffma2_rn(S, __ffma2_rn(S, f2(1.0f / 6.0f, 1.0f / 6.0f), f2(-0.5f, -0.5f)),
+                                                 f2(1.0f, 1.0f)));
+    const float2 omt = __ffma2_rn(t, f2(-1.0f, -1.0f), f2(1.0f, 1.0f));
+    const float2 den = f2(S.x < 0.0625f ? poly.x : omt.x, S.y < 0.0625f ? poly.y : omt.y);
+    const float2 num = __fadd2_rn(t, f2(1.0f, 1.0f));
+    const float2 d = __fadd2_rn(f2(s_lg2(num.x), s_lg2(num.y)), f2(-s_lg2(den.x), -s_lg2(den.y)));
+    return __fmul2_rn(d, f2(kSLn2, kSLn2));
+}
+
+template <int D, bool EXACT, typename MsgT>
+__device__ __forceinline__ void slot_check_pair(int dc, const int32_t *__restrict__ ent, int bZ, const float *A,
+                                                MsgT *Rc, int r, int Z, float X, float Xb, uint32_t (&pbad)[2])
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    float2 av[D];
+    int xo[D];
+    uint32_t sg0 = 0, sg1 = 0, par0 = 0, par1 = 0;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        if (EXACT || k < dc) {
+            const int e = ent[k];
+            int x = r + (e >> 16);
+            x -= (x >= Z) ? Z : 0;
+            xo[k] = x;
+            float ap[2], rv[2];
+            SMsg<float, 2>::ld(A + ((e & 0xffff) + x) * 2, ap);
+            SMsg<MsgT, 2>::ld(Rc + (bZ + k * Z + x) * 2, rv);
+            const float2 q = __ffma2_rn(f2(rv[0], rv[1]), f2(-1.0f, -1.0f), f2(ap[0], ap[1]));
+            par0 ^= __float_as_uint(ap[0]);
+            par1 ^= __float_as_uint(ap[1]);
+            const float2 m = psi_in2(f2(fminf(fabsf(q.x), X), fminf(fabsf(q.y), X)));
+            const uint32_t qs0 = __float_as_uint(q.x) & kSign, qs1 = __float_as_uint(q.y) & kSign;
+            sg0 ^= qs0;
+            sg1 ^= qs1;
+            av[k] = f2(__uint_as_float(__float_as_uint(fminf(m.x, Xb)) | qs0),
+                       __uint_as_float(__float_as_uint(fminf(m.y, Xb)) | qs1));
+        }
+    }
+    float2 sf[D + 1];
+    sf[D] = f2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = D - 1; k >= 0; k--)
+        sf[k] = (EXACT || k < dc) ? __fadd2_rn(sf[k + 1], f2(fabsf(av[k].x), fabsf(av[k].y))) : f2(0.0f, 0.0f);
+    float2 pre = f2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        if (EXACT || k < dc) {
+            const float2 mag = phi_out2(__fadd2_rn(pre, sf[k + 1]));
+            const float2 aa = f2(fabsf(av[k].x), fabsf(av[k].y));
+            pre = __fadd2_rn(pre, aa);
+            float out[2];
+            out[0] = __uint_as_float(__float_as_uint(fminf(mag.x, X)) | ((__float_as_uint(av[k].x) ^ sg0) & kSign));
+            out[1] = __uint_as_float(__float_as_uint(fminf(mag.y, X)) | ((__float_as_uint(av[k].y) ^ sg1) & kSign));
+            SMsg<MsgT, 2>::st(Rc + (bZ + k * Z + xo[k]) * 2, out);
+        }
+    }
+    pbad[0] |= par0;
+    pbad[1] |= par1;
+}
+
+#ifndef LDPC_SLOTS_PAIRED_FP
+#define LDPC_SLOTS_PAIRED_FP 1  // packed FP32x2 arithmetic for two codewords per thread
+#endif
+template <int D, bool EXACT, int V, typename MsgT>
+__device__ __forceinline__ void slot_check_v(int dc, const int32_t *__restrict__ ent, int bZ, const float *A, MsgT *Rc,
+                                             int r, int Z, float X, float Xb, uint32_t (&pbad)[V])
+{
+    if constexpr (V == 2 && LDPC_SLOTS_PAIRED_FP)
+        slot_check_pair<D, EXACT, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+    else
+        slot_check<D, EXACT, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+}
+
 template <int D, int DMAX, int V, typename MsgT>
 __device__ __forceinline__ void slot_check_dispatch(int dc, const int32_t *__restrict__ ent, int bZ, const float *A,
                                                     MsgT *Rc, int r, int Z, float X, float Xb, uint32_t (&pbad)[V])
 {
     if constexpr (D >= DMAX) {
-        slot_check<DMAX, false, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+        slot_check_v<DMAX, false, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
     } else if constexpr (D <= 8) {
         if (dc == D)
-            slot_check<D, true, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+            slot_check_v<D, true, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
         else
             slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
     } else {
         if (dc <= D)
-            slot_check<D, false, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+            slot_check_v<D, false, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
         else
             slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
     }
