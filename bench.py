@@ -443,10 +443,11 @@ def main():
 
     # roofline of the slot decoder (the headline form's only kernel): compute-bound; every
     # edge update needs two phi evaluations, i.e. at least two exponentials and two
-    # logarithms on the special-function units (16 per clock per SM)
+    # logarithms on the special-function units, whose throughput is measured live
     n_sl, sl_ms = ldpc.ldpc_profile_read("slots")
     edge_updates = args.steps * E * int(sum(int(it.sum()) for it in iters_np))
-    sfu_peak = n_sm * 16 * sm_mhz * 1e6 / 4 / 1e9                     # Gedge/s
+    ex2_s, lg2_s = ldpc.ldpc_sfu_throughput(stream)
+    sfu_peak = 1.0 / (2.0 / ex2_s + 2.0 / lg2_s) / 1e9                  # Gedge/s
     achieved = edge_updates / (sl_ms * 1e-3) / 1e9 if sl_ms > 0 else None
     traffic = None
     try:
@@ -458,7 +459,10 @@ def main():
         pass
     roofline = {"bound": "alu", "kernel": "k_flood_slots (on-chip flooding slot decoder)", "achieved": achieved,
                 "peak": sfu_peak, "unit": "Gedge/s", "frac": (achieved / sfu_peak) if achieved else None,
-                "peak_source": f"derived: {n_sm} SMs x 16 SFU ops/clk x {sm_mhz:.0f} MHz / 4 SFU ops per edge update",
+                "peak_source": (f"derived from the special-function throughput measured live on this GPU "
+                                f"(ex2 {ex2_s / 1e12:.2f} T/s = {ex2_s / n_sm / (sm_mhz * 1e6):.1f}/clk/SM, lg2 "
+                                f"{lg2_s / 1e12:.2f} T/s = {lg2_s / n_sm / (sm_mhz * 1e6):.1f}/clk/SM at {sm_mhz:.0f} MHz): "
+                                f"1 / (2/ex2 + 2/lg2) edge updates per second"),
                 "traffic": traffic, "launches": n_sl, "avg_launch_ms": sl_ms / max(n_sl, 1),
                 "algorithmic_work": "edge updates = E x iterations run, summed over codewords"}
 

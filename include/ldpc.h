@@ -267,6 +267,11 @@ ldpc_status ldpc_profile_enable(int32_t on);
 ldpc_status ldpc_profile_read(int32_t family, int64_t *launches, double *ms);
 ldpc_status ldpc_profile_reset(void);
 
+/* Measured special-function throughput of the current device in operations per second:
+ * independent ex2.approx and lg2.approx chains on every SM (the units the phi evaluations
+ * of the sum-product check rule run on).  Synchronizes `stream`; allocates 4 bytes. */
+ldpc_status ldpc_sfu_throughput(double *ex2_per_s, double *lg2_per_s, void *stream);
+
 /* Number of kernel launches the library has issued since the last reset (all families). */
 int64_t ldpc_launch_count(void);
 void ldpc_launch_count_reset(void);

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libldpc_gb300.so")
 SOURCES = ["ldpc_api.cu", "flood_kernels.cu", "flood_slots.cu", "layered_kernels.cu", "ldpc_static.cu",
-           "ldpc_session.cu"]
+           "ldpc_session.cu", "ldpc_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

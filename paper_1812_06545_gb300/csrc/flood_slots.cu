@@ -320,13 +320,14 @@ int slots_supported(const CodeDev &h, int msg) { return slots_for(h, msg, 1, tab
 
 int slots_pairable(const CodeDev &h, int msg) { return slots_for(h, msg, 2, tables_ints(h), max_smem_optin()) >= 2; }
 
-// Codewords per thread: two when pairing the slots of the first code costs no slot.
+// Codewords per thread: two when pairing the slots of the first code costs no slot and no
+// check has degree above 16 (high-degree checks keep too many values live per edge to pair).
 #ifndef LDPC_SLOTS_V
 #define LDPC_SLOTS_V 2
 #endif
 static int choose_v(const CodeDev &h, int msg, int tbl_ints, size_t limit)
 {
-    if (LDPC_SLOTS_V < 2) return 1;
+    if (LDPC_SLOTS_V < 2 || h.dc_max > 16) return 1;
     const int c1 = slots_for(h, msg, 1, tbl_ints, limit), c2 = slots_for(h, msg, 2, tbl_ints, limit);
     return (c2 >= 2 && c2 >= c1) ? 2 : 1;
 }
@@ -351,6 +352,9 @@ static cudaError_t launch_multi_d(int dmax, int V, const FloodMultiArgs &a, size
     if (dmax <= 16)
         return V == 2 ? launch_multi<16, 2, MsgT>(a, smem, threads, ctas, s)
                       : launch_multi<16, 1, MsgT>(a, smem, threads, ctas, s);
+    if (dmax <= 24)
+        return V == 2 ? launch_multi<24, 2, MsgT>(a, smem, threads, ctas, s)
+                      : launch_multi<24, 1, MsgT>(a, smem, threads, ctas, s);
     return V == 2 ? launch_multi<32, 2, MsgT>(a, smem, threads, ctas, s)
                   : launch_multi<32, 1, MsgT>(a, smem, threads, ctas, s);
 }
@@ -381,6 +385,7 @@ cudaError_t flood_multi_decode(const HostReq *reqs, int n, const ldpc_decode_par
     }
     const int tuned = codes[0]->tuned_flood[p.msg == LDPC_MSG_F16 ? 1 : 0];
     int V = tuned == SCHED_SLOTS_V2 ? 2 : tuned == SCHED_SLOTS_V1 ? 1 : choose_v(codes[0]->host, p.msg, tbl, limit);
+    if (!tuned && dmax > 16) V = 1;
     for (int g = 0; g < ng && V == 2; g++)
         if (slots_for(codes[g]->host, p.msg, 2, tbl, limit) < 2) V = 1;
     size_t smem = 0;

@@ -122,28 +122,68 @@ __device__ __forceinline__ void slot_check(int dc, const int32_t *__restrict__ e
             }
         }
     }
-    // exclusive sums from suffix and prefix sums of |a| (no cancellation)
-    float sf[D + 1][V];
+    if constexpr (D <= 8) {
+        // exclusive sums from suffix and prefix sums of |a| (no cancellation)
+        float sf[D + 1][V];
 #pragma unroll
-    for (int v = 0; v < V; v++) sf[D][v] = 0.0f;
+        for (int v = 0; v < V; v++) sf[D][v] = 0.0f;
 #pragma unroll
-    for (int k = D - 1; k >= 0; k--)
+        for (int k = D - 1; k >= 0; k--)
 #pragma unroll
-        for (int v = 0; v < V; v++) sf[k][v] = (EXACT || k < dc) ? sf[k + 1][v] + fabsf(av[k][v]) : 0.0f;
-    float pre[V];
+            for (int v = 0; v < V; v++) sf[k][v] = (EXACT || k < dc) ? sf[k + 1][v] + fabsf(av[k][v]) : 0.0f;
+        float pre[V];
 #pragma unroll
-    for (int v = 0; v < V; v++) pre[v] = 0.0f;
+        for (int v = 0; v < V; v++) pre[v] = 0.0f;
 #pragma unroll
-    for (int k = 0; k < D; k++) {
-        if (EXACT || k < dc) {
-            float out[V];
+        for (int k = 0; k < D; k++) {
+            if (EXACT || k < dc) {
+                float out[V];
 #pragma unroll
-            for (int v = 0; v < V; v++) {
-                const float mag = fminf(s_phi_out(pre[v] + sf[k + 1][v]), X);
-                pre[v] += fabsf(av[k][v]);
-                out[v] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
+                for (int v = 0; v < V; v++) {
+                    const float mag = fminf(s_phi_out(pre[v] + sf[k + 1][v]), X);
+                    pre[v] += fabsf(av[k][v]);
+                    out[v] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
+                }
+                SMsg<MsgT, V>::st(Rc + (bZ + k * Z + xo[k]) * V, out);
             }
-            SMsg<MsgT, V>::st(Rc + (bZ + k * Z + xo[k]) * V, out);
+        }
+    } else {
+        // high degree: S - a_k, except for an edge holding more than half of S (at most one),
+        // whose sum of the others is formed directly - no per-edge suffix array to hold
+        float S[V], amax[V], sx[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            S[v] = 0.0f;
+            amax[v] = 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < D; k++)
+            if (EXACT || k < dc)
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    S[v] += fabsf(av[k][v]);
+                    amax[v] = fmaxf(amax[v], fabsf(av[k][v]));
+                }
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+            float o = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; k++)
+                if (EXACT || k < dc) o += (fabsf(av[k][v]) == amax[v]) ? 0.0f : fabsf(av[k][v]);
+            sx[v] = (amax[v] > 0.5f * S[v]) ? o : S[v] - amax[v];
+        }
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            if (EXACT || k < dc) {
+                float out[V];
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    const float ak = fabsf(av[k][v]);
+                    const float mag = fminf(s_phi_out(ak == amax[v] ? sx[v] : S[v] - ak), X);
+                    out[v] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
+                }
+                SMsg<MsgT, V>::st(Rc + (bZ + k * Z + xo[k]) * V, out);
+            }
         }
     }
 #pragma unroll
@@ -209,22 +249,54 @@ __device__ __forceinline__ void slot_check_pair(int dc, const int32_t *__restric
                        __uint_as_float(__float_as_uint(fminf(m.y, Xb)) | qs1));
         }
     }
-    float2 sf[D + 1];
-    sf[D] = f2(0.0f, 0.0f);
+    if constexpr (D <= 8) {
+        float2 sf[D + 1];
+        sf[D] = f2(0.0f, 0.0f);
 #pragma unroll
-    for (int k = D - 1; k >= 0; k--)
-        sf[k] = (EXACT || k < dc) ? __fadd2_rn(sf[k + 1], f2(fabsf(av[k].x), fabsf(av[k].y))) : f2(0.0f, 0.0f);
-    float2 pre = f2(0.0f, 0.0f);
+        for (int k = D - 1; k >= 0; k--)
+            sf[k] = (EXACT || k < dc) ? __fadd2_rn(sf[k + 1], f2(fabsf(av[k].x), fabsf(av[k].y))) : f2(0.0f, 0.0f);
+        float2 pre = f2(0.0f, 0.0f);
 #pragma unroll
-    for (int k = 0; k < D; k++) {
-        if (EXACT || k < dc) {
-            const float2 mag = phi_out2(__fadd2_rn(pre, sf[k + 1]));
-            const float2 aa = f2(fabsf(av[k].x), fabsf(av[k].y));
-            pre = __fadd2_rn(pre, aa);
-            float out[2];
-            out[0] = __uint_as_float(__float_as_uint(fminf(mag.x, X)) | ((__float_as_uint(av[k].x) ^ sg0) & kSign));
-            out[1] = __uint_as_float(__float_as_uint(fminf(mag.y, X)) | ((__float_as_uint(av[k].y) ^ sg1) & kSign));
-            SMsg<MsgT, 2>::st(Rc + (bZ + k * Z + xo[k]) * 2, out);
+        for (int k = 0; k < D; k++) {
+            if (EXACT || k < dc) {
+                const float2 mag = phi_out2(__fadd2_rn(pre, sf[k + 1]));
+                const float2 aa = f2(fabsf(av[k].x), fabsf(av[k].y));
+                pre = __fadd2_rn(pre, aa);
+                float out[2];
+                out[0] = __uint_as_float(__float_as_uint(fminf(mag.x, X)) | ((__float_as_uint(av[k].x) ^ sg0) & kSign));
+                out[1] = __uint_as_float(__float_as_uint(fminf(mag.y, X)) | ((__float_as_uint(av[k].y) ^ sg1) & kSign));
+                SMsg<MsgT, 2>::st(Rc + (bZ + k * Z + xo[k]) * 2, out);
+            }
+        }
+    } else {
+        // high degree: S - a_k with the dominant edge's sum formed directly (see slot_check)
+        float2 S = f2(0.0f, 0.0f);
+        float m0 = 0.0f, m1 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; k++)
+            if (EXACT || k < dc) {
+                S = __fadd2_rn(S, f2(fabsf(av[k].x), fabsf(av[k].y)));
+                m0 = fmaxf(m0, fabsf(av[k].x));
+                m1 = fmaxf(m1, fabsf(av[k].y));
+            }
+        float o0 = 0.0f, o1 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; k++)
+            if (EXACT || k < dc) {
+                o0 += (fabsf(av[k].x) == m0) ? 0.0f : fabsf(av[k].x);
+                o1 += (fabsf(av[k].y) == m1) ? 0.0f : fabsf(av[k].y);
+            }
+        const float x0 = (m0 > 0.5f * S.x) ? o0 : S.x - m0, x1 = (m1 > 0.5f * S.y) ? o1 : S.y - m1;
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            if (EXACT || k < dc) {
+                const float a0 = fabsf(av[k].x), a1 = fabsf(av[k].y);
+                const float2 mag = phi_out2(f2(a0 == m0 ? x0 : S.x - a0, a1 == m1 ? x1 : S.y - a1));
+                float out[2];
+                out[0] = __uint_as_float(__float_as_uint(fminf(mag.x, X)) | ((__float_as_uint(av[k].x) ^ sg0) & kSign));
+                out[1] = __uint_as_float(__float_as_uint(fminf(mag.y, X)) | ((__float_as_uint(av[k].y) ^ sg1) & kSign));
+                SMsg<MsgT, 2>::st(Rc + (bZ + k * Z + xo[k]) * 2, out);
+            }
         }
     }
     pbad[0] |= par0;

@@ -90,6 +90,7 @@ def lib():
             "ldpc_session_cancel": [vp, C.c_uint64],
             "ldpc_session_pause": [vp, i32],
             "ldpc_session_stats_get": [vp, vp],
+            "ldpc_sfu_throughput": [vp, vp, vp],
             "ldpc_profile_enable": [i32],
             "ldpc_profile_read": [i32, vp, vp],
             "ldpc_profile_reset": [],
@@ -253,6 +254,13 @@ def ldpc_session_stats_get(sess: int) -> SessionStats:
 
 def ldpc_session_destroy(sess: int) -> None:
     lib().ldpc_session_destroy(sess)
+
+
+def ldpc_sfu_throughput(stream=None) -> tuple[float, float]:
+    """Measured (ex2, lg2) special-function operations per second of the current device."""
+    a, b = C.c_double(), C.c_double()
+    _check(lib().ldpc_sfu_throughput(C.byref(a), C.byref(b), _stream(stream)), "ldpc_sfu_throughput")
+    return a.value, b.value
 
 
 def ldpc_multi_workspace_size() -> int:
