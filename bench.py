@@ -34,8 +34,32 @@ sys.path.insert(0, ROOT)
 METRIC = "decoded info Gbit/s and p99 latency at equal FER vs plain FP32 flooding SPA, 1 GB300"
 WORKLOAD = "flood_n1944_b8192_sweep"
 LAYERED_WORKLOAD = "layered_i8_n1944_r56_b65536"
-CN_SOURCE = os.path.join(ROOT, "paper_1812_06545_gb300", "csrc", "flood_kernels.cu")
-SLOTS_SOURCE = os.path.join(ROOT, "paper_1812_06545_gb300", "csrc", "flood_slots.cu")
+_CSRC = os.path.join(ROOT, "paper_1812_06545_gb300", "csrc")
+# the files each profiled kernel is compiled from: a stored ncu traffic figure is used only
+# while their combined hash is unchanged
+CN_SOURCES = ("flood_kernels.cu", "ldpc_internal.h")
+SLOTS_SOURCES = ("flood_slots.cu", "slot_common.cuh", "ldpc_internal.h")
+
+
+def source_sha256(names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(_CSRC, n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def stored_traffic(kernel, sources):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or None when the
+    kernel's sources changed since the capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            ent = json.load(f).get(kernel)
+        if ent and ent.get("source_sha256") == source_sha256(sources):
+            return ent.get("bytes_per_launch_full_size")
+    except (OSError, ValueError):
+        pass
+    return None
 
 
 def streaming_roofline(ldpc, iters_np, steps, N, E, T, hbm_peak, peak_src):
@@ -51,14 +75,7 @@ def streaming_roofline(ldpc, iters_np, steps, N, E, T, hbm_peak, peak_src):
             vn_bytes += int((it >= t).sum()) * (4 * E + 8 * N)
     cn_gbs = steps * cn_bytes / (cn_ms * 1e-3) / 1e9 if cn_ms > 0 else None
     vn_gbs = steps * vn_bytes / (vn_ms * 1e-3) / 1e9 if vn_ms > 0 else None
-    traffic = None
-    try:
-        tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
-        ent = tr.get("k_flood_cn")
-        if ent and ent.get("source_sha256") == hashlib.sha256(open(CN_SOURCE, "rb").read()).hexdigest():
-            traffic = ent.get("bytes_per_launch_full_size")
-    except Exception:
-        pass
+    traffic = stored_traffic("k_flood_cn", CN_SOURCES)
     return {"bound": "hbm", "kernel": "k_flood_cn (check-node phase)", "achieved": cn_gbs, "peak": hbm_peak,
             "unit": "GB/s", "frac": (cn_gbs / hbm_peak) if cn_gbs else None, "peak_source": peak_src,
             "traffic": traffic, "launches": n_cn, "avg_launch_ms": cn_ms / max(n_cn, 1),
@@ -449,14 +466,7 @@ def main():
     ex2_s, lg2_s = ldpc.ldpc_sfu_throughput(stream)
     sfu_peak = 1.0 / (2.0 / ex2_s + 2.0 / lg2_s) / 1e9                  # Gedge/s
     achieved = edge_updates / (sl_ms * 1e-3) / 1e9 if sl_ms > 0 else None
-    traffic = None
-    try:
-        tr = json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
-        ent = tr.get("k_flood_slots")
-        if ent and ent.get("source_sha256") == hashlib.sha256(open(SLOTS_SOURCE, "rb").read()).hexdigest():
-            traffic = ent.get("bytes_per_launch_full_size")
-    except Exception:
-        pass
+    traffic = stored_traffic("k_flood_slots", SLOTS_SOURCES)
     roofline = {"bound": "alu", "kernel": "k_flood_slots (on-chip flooding slot decoder)", "achieved": achieved,
                 "peak": sfu_peak, "unit": "Gedge/s", "frac": (achieved / sfu_peak) if achieved else None,
                 "peak_source": (f"derived from the special-function throughput measured live on this GPU "
