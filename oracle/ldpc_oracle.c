@@ -13,9 +13,10 @@
  *     passing; Algorithm 1 loop order: init, CN->VN, VN->CN, hard decision) in FP64, with
  *     the phi-domain check rule and a clamp on |Q| (the paper gives no formulas; the
  *     textbook rule it cites is written out below);
- *   - horizontal layered normalised min-sum (Sec. II, "Algorithm 2": every check of a
- *     layer is computed from the current variable values and those values are updated at
- *     once) in saturated integer arithmetic;
+ *   - horizontal layered decoding (Sec. II, "Algorithm 2": every check of a layer is
+ *     computed from the current variable values and those values are updated at once),
+ *     with the sum-product rule in FP64 and with normalised min-sum in saturated integer
+ *     arithmetic;
  *   - syndrome H.c, dual-diagonal encoding, brute-force maximum-likelihood decoding.
  *
  * Parity pins: every function here is checked by the CPU tests against facts that do
@@ -346,6 +347,107 @@ static int check_layers(int M, int N, const int32_t *rp, const int32_t *ci, int 
             }
     }
     free(seen);
+    return rc;
+}
+
+/* Horizontal layered sum-product in FP64 (Sec. II "Algorithm 2" schedule with the
+ * sum-product check rule of Sec. I): the checks of a layer are computed from the current
+ * posteriors, and those posteriors are updated at once.
+ *
+ *   init : APP_n = L_n, R_mn = 0
+ *   for t = 1..max_iter:
+ *     for each layer l in order, for each check m of l:
+ *       Q_n   = APP_n - R_mn                                      for n in N(m)
+ *       R'_mn = prod_{n' != n} sgn(Q_n') * min(X, phi( sum_{n' != n} phi(clampX |Q_n'|) ))
+ *               (exclusive sum and product formed directly; rounded to binary16 if fp16_msgs)
+ *       APP_n = Q_n + R'_mn;  R_mn <- R'_mn
+ *     HD : c_n = [APP_n < 0];  exit as in orc_spa_flood.
+ * The check rule, clamp and exit are those of orc_spa_flood; only the schedule differs.
+ * Outputs as orc_spa_flood (R_out in CSR edge order, may be NULL). */
+int orc_spa_layered(int M, int N, const int32_t *rp, const int32_t *ci, int nl, const int32_t *lp,
+                    const float *L, int64_t B, int max_iter, int early_exit, double X, int fp16_msgs,
+                    double *app_out, uint8_t *bits_out, int32_t *iters_out, double *R_out, int nthreads)
+{
+    if (max_iter < 1 || !(X > 1.0) || check_csr(M, N, rp, ci) != ORC_OK) return ORC_EINVAL;
+    int lrc = check_layers(M, N, rp, ci, nl, lp);
+    if (lrc != ORC_OK) return lrc;
+    const int E = rp[M];
+    const int dmax = max_row_degree(M, rp);
+    const double phiX = phi(X);
+    int rc = ORC_OK;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        double *app = (double *)malloc(sizeof(double) * N);
+        double *R = (double *)malloc(sizeof(double) * E);
+        double *Q = (double *)malloc(sizeof(double) * dmax);
+        double *Rn = (double *)malloc(sizeof(double) * dmax);
+        uint8_t *hd = (uint8_t *)malloc(N);
+        const int ok = app && R && Q && Rn && hd;
+        if (!ok) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            rc = ORC_ENOMEM;
+        }
+        {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+            for (int64_t b = 0; b < B; b++) {
+                if (!ok) continue;
+                const float *Lb = L + b * (int64_t)N;
+                for (int n = 0; n < N; n++) app[n] = (double)Lb[n];
+                for (int e = 0; e < E; e++) R[e] = 0.0;
+                int iters = max_iter;
+                for (int t = 1; t <= max_iter; t++) {
+                    for (int l = 0; l < nl; l++) {
+                        for (int m = lp[l]; m < lp[l + 1]; m++) {
+                            int e0 = rp[m], dc = rp[m + 1] - rp[m];
+                            for (int k = 0; k < dc; k++) Q[k] = app[ci[e0 + k]] - R[e0 + k];
+                            for (int k = 0; k < dc; k++) {
+                                double sgn = 1.0, sum = 0.0;
+                                for (int k2 = 0; k2 < dc; k2++) {
+                                    if (k2 == k) continue;
+                                    if (Q[k2] < 0.0) sgn = -sgn;
+                                    double a = fabs(Q[k2]);
+                                    if (a < phiX) a = phiX;
+                                    if (a > X) a = X;
+                                    sum += phi(a);
+                                }
+                                double mag = phi(sum);
+                                if (mag > X) mag = X;
+                                double r = sgn * mag;
+                                Rn[k] = fp16_msgs ? round_binary16(r) : r;
+                            }
+                            for (int k = 0; k < dc; k++) {
+                                R[e0 + k] = Rn[k];
+                                app[ci[e0 + k]] = Q[k] + Rn[k];
+                            }
+                        }
+                    }
+                    for (int n = 0; n < N; n++) hd[n] = app[n] < 0.0;
+                    if (early_exit && syndrome_weight(M, rp, ci, hd) == 0) {
+                        iters = t;
+                        break;
+                    }
+                }
+                if (app_out)
+                    for (int n = 0; n < N; n++) app_out[b * (int64_t)N + n] = app[n];
+                for (int n = 0; n < N; n++) bits_out[b * (int64_t)N + n] = hd[n];
+                if (R_out)
+                    for (int e = 0; e < E; e++) R_out[b * (int64_t)E + e] = R[e];
+                iters_out[b] = iters;
+            }
+        }
+        free(app);
+        free(R);
+        free(Q);
+        free(Rn);
+        free(hd);
+    }
     return rc;
 }
 

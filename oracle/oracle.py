@@ -133,6 +133,25 @@ class Code:
                "spa_flood")
         return (app, bits, iters, R) if return_messages else (app, bits, iters)
 
+    def spa_layered(self, L, max_iter: int, early_exit: bool = True, X: float = 80.0, fp16_msgs: bool = False,
+                    nthreads: int = 0, return_messages: bool = False):
+        """FP64 layered sum-product over ``self.layers``: same inputs and outputs as spa_flood."""
+        if self.layers is None:
+            raise ValueError("code has no layer boundaries")
+        L = np.ascontiguousarray(np.atleast_2d(L), dtype=np.float32)
+        B = L.shape[0]
+        app = np.empty((B, self.N), dtype=np.float64)
+        bits = np.empty((B, self.N), dtype=np.uint8)
+        iters = np.empty(B, dtype=np.int32)
+        R = np.empty((B, self.E), dtype=np.float64) if return_messages else None
+        _check(lib().orc_spa_layered(C.c_int(self.M), C.c_int(self.N), _p(self.rp), _p(self.ci),
+                                     C.c_int(len(self.layers) - 1), _p(self.layers), _p(L), C.c_int64(B),
+                                     C.c_int(max_iter), C.c_int(int(early_exit)), C.c_double(X),
+                                     C.c_int(int(fp16_msgs)), _p(app), _p(bits), _p(iters),
+                                     None if R is None else _p(R), C.c_int(nthreads)),
+               "spa_layered")
+        return (app, bits, iters, R) if return_messages else (app, bits, iters)
+
     def incoming_message_sum(self, R):
         """sum_m |R_mn| per variable n, for messages R [B, E] in CSR edge order."""
         out = np.zeros((R.shape[0], self.N))

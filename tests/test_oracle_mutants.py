@@ -34,9 +34,21 @@ MUTANTS = [
     ("nms_no_app_sat", "app[ci[e0 + k]] = sat(Q[k] + R[e0 + k], app_sat);", "app[ci[e0 + k]] = Q[k] + R[e0 + k];", 0),
     ("nms_min_swapped", "int32_t mag = (k == arg) ? min2 : min1;", "int32_t mag = (k == arg) ? min1 : min2;", 0),
     ("nms_exit_inverted", "if (early_exit && syndrome_weight(M, rp, ci, hd) == 0) {",
-     "if (early_exit && syndrome_weight(M, rp, ci, hd) != 0) {", 1),
+     "if (early_exit && syndrome_weight(M, rp, ci, hd) != 0) {", 2),
     ("nms_layers_reversed", "for (int l = 0; l < nl; l++) {\n                        for (int m = lp[l];",
+     "for (int l = nl - 1; l >= 0; l--) {\n                        for (int m = lp[l];", 1),
+    # layered sum-product (second occurrence of the lines it shares with the flooding routine)
+    ("spal_sign_flipped", "double r = sgn * mag;", "double r = -sgn * mag;", 1),
+    ("spal_no_extrinsic", "Q[k] = app[ci[e0 + k]] - R[e0 + k];", "Q[k] = app[ci[e0 + k]];", 1),
+    ("spal_app_from_channel", "app[ci[e0 + k]] = Q[k] + Rn[k];", "app[ci[e0 + k]] = (double)Lb[ci[e0 + k]] + Rn[k];", 0),
+    ("spal_messages_not_kept", "R[e0 + k] = Rn[k];\n", "\n", 0),
+    ("spal_layers_reversed", "for (int l = 0; l < nl; l++) {\n                        for (int m = lp[l];",
      "for (int l = nl - 1; l >= 0; l--) {\n                        for (int m = lp[l];", 0),
+    ("spal_fp16_ignored", "Rn[k] = fp16_msgs ? round_binary16(r) : r;", "Rn[k] = r;", 0),
+    ("spal_no_upper_clamp", "if (a > X) a = X;", "", 1),
+    ("spal_exit_inverted", "if (early_exit && syndrome_weight(M, rp, ci, hd) == 0) {",
+     "if (early_exit && syndrome_weight(M, rp, ci, hd) != 0) {", 1),
+    ("spal_hard_decision", "hd[n] = app[n] < 0.0;", "hd[n] = app[n] > 0.0;", 1),
     ("encoder_p1_shift", "p[1 * Z + r] = lam[r] ^ p[(r + s_top) % Z];", "p[1 * Z + r] = lam[r] ^ p[r];", 0),
     ("encoder_transposed_shift", "lam[i * Z + r] ^= ub[j * Z + (r + s) % Z] & 1;",
      "lam[i * Z + r] ^= ub[j * Z + (r + Z - s) % Z] & 1;", 0),
