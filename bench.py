@@ -97,6 +97,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="arrival window per offered rate")
+    ap.add_argument("--no-paper-shape", action="store_true", help="skip the frame-length / stream sweep")
+    ap.add_argument("--no-equal-fer", action="store_true", help="skip the equal-FER throughput comparison")
+    ap.add_argument("--fer-frames", type=int, default=400000, help="frames per equal-FER point")
     return ap.parse_args()
 
 
@@ -296,6 +299,159 @@ def run_serving(ldpc, dev, window_s: float):
 
 # ------------------------------------------------------------------ reference arm (the oracle)
 
+# rate-1/2 codes at the frame lengths of the paper's throughput figures (Sec. IV)
+PAPER_SHAPE_CODES = ["qc12x24_z24_s6", "qc16x32_z32_s7", "qc12x24_z50_s8", "qc12x24_z81_s2", "qc12x24_z96_s9",
+                     "qc10x20_z200_s10", "qc20x40_z200_s11"]
+
+
+def run_paper_shape(ldpc, dev, reps: int = 3):
+    """Throughput over frame length for a fixed number of layered iterations (5 and 10, no
+    early exit), the shape of the paper's Sec. IV measurements: end to end through the host
+    API (pinned LLRs in, decisions out, copies included) with W = 1 and W = 3 streams, and the
+    device-resident decode alone.  2^24 coded bits per run, 2.0 dB."""
+    import torch
+
+    from paper_1812_06545_gb300 import inputs as I
+
+    out = []
+    stream = torch.cuda.current_stream(dev)
+    for name in PAPER_SHAPE_CODES:
+        B, Z = I.load_code(name)
+        code = ldpc.Code(B, Z)
+        n = (1 << 24) // code.N
+        _, _, c, L = I.make_frames(name, n, 2.0, 71, 72)
+        Lh = torch.from_numpy(L).pin_memory()
+        bh = torch.empty((n, code.N), dtype=torch.uint8).pin_memory()
+        ih = torch.empty((n,), dtype=torch.int32).pin_memory()
+        Ld = Lh.to(dev)
+        bd = torch.empty((n, code.N), dtype=torch.uint8, device=dev)
+        idv = torch.empty((n,), dtype=torch.int32, device=dev)
+        chunk = (n + 11) // 12
+        for form in ("layered_f32", "layered_i8"):
+            for T in (5, 10):
+                p = ldpc.params_for(form, max_iter=T, early_exit=0)
+                wsb = ldpc.ldpc_workspace_size(code.handle, p, n)
+                ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+                times = []
+                for r in range(reps + 1):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ldpc.ldpc_decode_batch(code.handle, p, Ld, ldpc.LDPC_LLR_F32, n, bd, idv, None, ws, wsb, stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    if r:
+                        times.append(e0.elapsed_time(e1) * 1e-3)
+                row = {"code": name, "N": code.N, "K": code.K, "codewords": n, "form": form, "iterations": T,
+                       "device_info_gbps": n * code.K / float(np.median(times)) / 1e9}
+                for W in (1, 3):
+                    times = []
+                    for r in range(reps + 1):
+                        t0 = time.perf_counter()
+                        ldpc.ldpc_decode_host(code.handle, p, Lh, n, bh, ih, n_streams=W, chunk_cw=chunk)
+                        if r:
+                            times.append(time.perf_counter() - t0)
+                    row[f"e2e_info_gbps_w{W}"] = n * code.K / float(np.median(times)) / 1e9
+                row["fer"] = float((bh.numpy() != c).any(axis=1).mean())
+                out.append(row)
+        ldpc.ldpc_release_host_buffers()
+        del code
+    return {"what": "info Gbit/s over frame length, fixed layered iterations (no early exit), 2^24 coded bits per "
+                    "run at 2.0 dB; e2e through ldpc_decode_host with W streams (12 chunks), device = decode of "
+                    "HBM-resident LLRs", "rows": out}
+
+
+def run_equal_fer(ldpc, dev, n_frames: int = 400000, chunk: int = 50000):
+    """Throughput at equal frame error rate.  For each code: E* = the Eb/N0 where FP32
+    flooding (max 20 iterations, early exit) has FER 1e-3 (sweep, then log-FER interpolated
+    in dB); at E* the plain FP32 comparator is measured on n_frames frames, and every other
+    form gets the smallest max_iter on a ladder whose FER is within 10 % of the comparator's;
+    its throughput there over the comparator's is the ratio.  Frames: codewords from an
+    encoded pool of 8192, BPSK/AWGN noise drawn on the device (seeded), the same frames for
+    every form at a point.  Device-resident decode timed with CUDA events."""
+    import torch
+
+    from paper_1812_06545_gb300 import inputs as I
+
+    stream = torch.cuda.current_stream(dev)
+    ladder = (4, 5, 6, 8, 10, 12, 15, 20, 30, 50)
+
+    def frames(pool, rate, eb, seed, n):
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        idx = torch.arange(n, device=dev) % pool.shape[0]
+        x = 1.0 - 2.0 * pool[idx].float()
+        s2 = 1.0 / (2.0 * rate * 10.0 ** (eb / 10.0))
+        y = x + (s2 ** 0.5) * torch.randn(x.shape, generator=g, device=dev)
+        return (2.0 / s2) * y, idx
+
+    def measure(code, pool, rate, form, eb, max_iter, n, seed0):
+        p = ldpc.params_for(form, max_iter=max_iter, early_exit=1)
+        errs, ms, it_sum = 0, 0.0, 0
+        for k in range(0, n, chunk):
+            m = min(chunk, n - k)
+            L, idx = frames(pool, rate, eb, seed0 + k // chunk, m)
+            bits = torch.empty((m, code.N), dtype=torch.uint8, device=dev)
+            iters = torch.empty((m,), dtype=torch.int32, device=dev)
+            wsb = ldpc.ldpc_workspace_size(code.handle, p, m)
+            ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ldpc.ldpc_decode_batch(code.handle, p, L, ldpc.LDPC_LLR_F32, m, bits, iters, None, ws, wsb, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            errs += int((bits != pool[idx]).any(dim=1).sum())
+            it_sum += int(iters.sum())
+        return {"fer": errs / n, "errors": errs, "frames": n, "max_iter": max_iter, "avg_iterations": it_sum / n,
+                "info_gbps": n * code.K / (ms * 1e-3) / 1e9}
+
+    out = []
+    for name, forms in (("qc12x24_z81_s2", ("flood_f32", "flood_f16", "layered_f32", "layered_f16", "layered_i8")),
+                        ("qc4x24_z81_s3", ("flood_f32", "flood_f16", "layered_f32", "layered_i8"))):
+        B, Z, c, _ = I.make_frames(name, 8192, 3.0, 81, 82)
+        code = ldpc.Code(B, Z)
+        pool = torch.from_numpy(c).to(dev)
+        rate = code.K / code.N
+        # E*: FER of FP32 flooding over a coarse sweep (n_frames / 4 frames per point)
+        pts = []
+        eb = 1.5 if rate < 0.6 else 3.0
+        while eb < 8.0:
+            r = measure(code, pool, rate, "flood_f32", eb, 20, n_frames // 4, 1000)
+            pts.append((eb, r["fer"]))
+            if r["fer"] < 1e-3:
+                if len(pts) > 1:
+                    break
+                pts, eb = [], eb - 1.0          # started above E*: restart lower
+                continue
+            eb += 0.25
+        (e_a, f_a), (e_b, f_b) = pts[-2], pts[-1]
+        if f_b > 0 and f_a > 0:
+            e_star = e_a + (np.log(1e-3) - np.log(f_a)) / (np.log(f_b) - np.log(f_a)) * (e_b - e_a)
+        else:
+            e_star = e_b
+        ref = measure(code, pool, rate, "plain_f32", e_star, 20, n_frames, 2000)
+        ref["form"] = "plain_f32"
+        rows = []
+        for form in forms:
+            best = None
+            for T in ladder:
+                r = measure(code, pool, rate, form, e_star, T, n_frames, 2000)
+                best = r
+                if r["fer"] <= 1.1 * ref["fer"]:
+                    break
+            best["form"] = form
+            best["fer_within_10pct"] = bool(best["fer"] <= 1.1 * ref["fer"])
+            best["ratio_vs_plain_f32"] = best["info_gbps"] / ref["info_gbps"]
+            rows.append(best)
+        out.append({"code": name, "N": code.N, "K": code.K, "ebn0_star_db": float(e_star),
+                    "sweep_fp32_flooding": [{"ebn0_db": e, "fer": f} for e, f in pts], "reference": ref,
+                    "forms": rows})
+        del code
+    return {"what": "info Gbit/s at equal FER: E* where FP32 flooding (max 20, early exit) has FER 1e-3; each "
+                    "form at the smallest max_iter whose FER is within 10 % of the plain FP32 comparator's at E*",
+            "codes": out}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -492,19 +648,29 @@ def main():
     # ---------------- other forms on the same inputs
     if not args.no_forms:
         forms = {}
-        for form in ("flood_f16", "stream_f32", "stream_f16", "plain_f32"):
-            prof = form.startswith("stream")
+        # on-chip forms: special-function roofline of their slot kernel (same peak as above)
+        sfu_family = {"flood_f16": "slots", "layered_f32": "layered_spa", "layered_f16": "layered_spa"}
+        for form in ("flood_f16", "layered_f32", "layered_f16", "stream_f32", "stream_f16", "plain_f32"):
+            prof = form.startswith("stream") or form in sfu_family
             fms, fl, fb, fi = run_form(form, args.steps, args.warmup, profile=prof)
             fms = max_over_ranks(fms)
             fv = units * code.K / (fms * 1e-3) / 1e9
+            fi_np = [x.cpu().numpy() for x in fi]
             ffer = {f"{eb:.2f}": float((b.cpu().numpy() != c).any(axis=1).mean()) for (eb, c, _), b in zip(frames, fb)}
-            forms[form] = {"value": fv, "ms_per_step": fms / args.steps, "fer": ffer, "gpu_launches": fl}
-            if prof:
-                forms[form]["roofline"] = streaming_roofline(ldpc, [x.cpu().numpy() for x in fi], args.steps, N, E, T,
-                                                             hbm_peak, peak_src)
+            forms[form] = {"value": fv, "ms_per_step": fms / args.steps, "fer": ffer, "gpu_launches": fl,
+                           "avg_iterations": float(np.mean(np.concatenate(fi_np)))}
+            if form.startswith("stream"):
+                forms[form]["roofline"] = streaming_roofline(ldpc, fi_np, args.steps, N, E, T, hbm_peak, peak_src)
+            elif form in sfu_family:
+                fn, fk_ms = ldpc.ldpc_profile_read(sfu_family[form])
+                fach = args.steps * E * int(sum(int(it.sum()) for it in fi_np)) / (fk_ms * 1e-3) / 1e9 \
+                    if fk_ms > 0 else None
+                forms[form]["roofline"] = {"bound": "alu", "achieved": fach, "peak": sfu_peak, "unit": "Gedge/s",
+                                           "frac": (fach / sfu_peak) if fach else None, "launches": fn,
+                                           "avg_launch_ms": fk_ms / max(fn, 1)}
         plain = forms["plain_f32"]["value"]
         forms["flood_f32"] = {"value": value, "vs_plain_f32": value / plain}
-        for f in ("flood_f16", "stream_f32", "stream_f16"):
+        for f in ("flood_f16", "layered_f32", "layered_f16", "stream_f32", "stream_f16"):
             forms[f]["vs_plain_f32"] = forms[f]["value"] / plain
         # int8 layered min-sum on its own workload (rate 5/6, 65536 codewords, 4.0 dB)
         lw, LB, LZ, lframes = workload_frames(LAYERED_WORKLOAD, rank)
@@ -597,6 +763,14 @@ def main():
     # ---------------- serving loop: Poisson arrivals of mixed requests (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_serving:
         line["serving"] = run_serving(ldpc, dev, args.serve_seconds)
+
+    # ---------------- equal-FER comparison (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_equal_fer:
+        line["equal_fer"] = run_equal_fer(ldpc, dev, args.fer_frames)
+
+    # ---------------- paper-shape sweep: frame length x iterations x streams (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_paper_shape:
+        line["paper_shape"] = run_paper_shape(ldpc, dev)
 
     # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

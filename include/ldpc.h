@@ -63,7 +63,12 @@ typedef enum {
 typedef struct ldpc_code ldpc_code;
 
 /* Decoder parameters.  Supported forms:
- *   sched FLOODING + algo SPA + msg F32 or F16  (sum-product, messages stored in HBM)
+ *   sched FLOODING + algo SPA + msg F32 or F16  (sum-product; Algorithm 1 order)
+ *   sched LAYERED  + algo SPA + msg F32 or F16  (sum-product on the layered schedule of
+ *                                                "Algorithm 2": block rows in order, each
+ *                                                computed from the current posteriors and
+ *                                                updating them at once; impl AUTO only, for
+ *                                                codes whose slot fits in shared memory)
  *   sched LAYERED  + algo NMS + msg I8          (bit-exact integer normalised min-sum)
  * Every field must be set; ldpc_default_params() fills the defaults below. */
 typedef struct {
@@ -127,8 +132,8 @@ ldpc_status ldpc_decode_batch(const ldpc_code *code, const ldpc_decode_params *p
 /* Choose, by timing, the schedule ldpc_decode_batch / ldpc_decode_multi use for this code
  * and form with impl AUTO, and remember it in the code object.
  *   Flooding forms: the on-chip slot decoder with one or two codewords per thread (where
- *   the code fits), or the HBM-streaming kernels.  Layered form: persistent slots or the
- *   fixed group per CTA.
+ *   the code fits), or the HBM-streaming kernels.  Layered min-sum: persistent slots or the
+ *   fixed group per CTA.  The layered sum-product has one schedule: LDPC_ENOTSUP.
  *   llr_dev / llr_type / n_cw  a representative device sample of the workload (>= 1 codeword).
  *   choice     receives the pick: 1 slots (1 codeword per thread), 2 slots (2 per thread),
  *              3 streaming / fixed group (may be NULL).
@@ -262,7 +267,8 @@ void ldpc_release_host_buffers(void);
  * events on its launch stream; ldpc_profile_read returns, per kernel family, the number
  * of launches and the summed event time in milliseconds (it synchronizes the pending
  * events).  Families: 0 interleave, 1 check-node, 2 variable-node, 3 deinterleave,
- * 4 layered, 5 plain check-node, 6 plain variable-node, 7 on-chip flooding slot decoder. */
+ * 4 layered min-sum, 5 plain check-node, 6 plain variable-node, 7 on-chip flooding slot
+ * decoder, 8 on-chip layered sum-product slot decoder. */
 ldpc_status ldpc_profile_enable(int32_t on);
 ldpc_status ldpc_profile_read(int32_t family, int64_t *launches, double *ms);
 ldpc_status ldpc_profile_reset(void);
@@ -271,6 +277,19 @@ ldpc_status ldpc_profile_reset(void);
  * independent ex2.approx and lg2.approx chains on every SM (the units the phi evaluations
  * of the sum-product check rule run on).  Synchronizes `stream`; allocates 4 bytes. */
 ldpc_status ldpc_sfu_throughput(double *ex2_per_s, double *lg2_per_s, void *stream);
+
+/* Device status word: the decoding kernels flag bad channel input without a host pass over
+ * the data.  Bits: 1 = a non-finite fp32 LLR was decoded (NaN or infinity; the decode ran
+ * on it as given), 2 = an int8 LLR outside [-msg_sat, msg_sat] was decoded (it was
+ * saturated to the range).  The word is per device and shared by every stream and thread on
+ * it.  ldpc_stream_check orders itself after the work queued on `stream`, takes the word
+ * (swapping in zero, so no flag set concurrently is lost) and synchronizes the stream.
+ *   flags  receives the bits taken (may be NULL).
+ * Returns LDPC_OK when no bit was set, LDPC_EINVAL (with a message naming the bits) when
+ * one was, LDPC_ECUDA if the stream or the copy failed.  Allocates nothing after the first
+ * code was created on the device.  (An input check of the boundary; the paper's decoder has
+ * no counterpart.) */
+ldpc_status ldpc_stream_check(void *stream, uint32_t *flags);
 
 /* Number of kernel launches the library has issued since the last reset (all families). */
 int64_t ldpc_launch_count(void);

@@ -175,7 +175,7 @@ __device__ __forceinline__ void ld_i(const int32_t *p, int (&x)[V])
 // Block: 32 nodes x TILE codewords through shared memory, both sides coalesced.
 __global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ llr, int64_t n_cw, int N,
                                                     float *__restrict__ L, int32_t *__restrict__ done_at,
-                                                    int32_t *__restrict__ unsat)
+                                                    int32_t *__restrict__ unsat, unsigned int *status)
 {
     __shared__ float sm[TILE][33];
     const int tile = blockIdx.y, n0 = blockIdx.x * 32;
@@ -183,7 +183,9 @@ __global__ void __launch_bounds__(256) k_interleave(const float *__restrict__ ll
     for (int c = w; c < TILE; c += 8) {
         const int64_t cw = (int64_t)tile * TILE + c;
         const int n = n0 + lane;
-        sm[c][lane] = (cw < n_cw && n < N) ? __ldg(llr + cw * N + n) + 0.0f : 0.0f;  // -0 -> +0
+        const float v = (cw < n_cw && n < N) ? __ldg(llr + cw * N + n) : 0.0f;
+        if (!isfinite(v)) atomicOr(status, IN_NONFINITE);
+        sm[c][lane] = v + 0.0f;  // -0 -> +0
     }
     __syncthreads();
     for (int nn = w; nn < 32; nn += 8) {
@@ -602,7 +604,7 @@ cudaError_t flood_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_p
     const dim3 tgrid((unsigned)((h.N + 31) / 32), (unsigned)ntiles);
     {
         LaunchScope ls(F_INTERLEAVE, s);
-        k_interleave<<<tgrid, 256, 0, s>>>(llr, n_cw, h.N, ws.L, ws.done_at, ws.unsat);
+        k_interleave<<<tgrid, 256, 0, s>>>(llr, n_cw, h.N, ws.L, ws.done_at, ws.unsat, h.status);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

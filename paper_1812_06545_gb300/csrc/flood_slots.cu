@@ -133,7 +133,10 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                     if (j0 + u < nb) x[u] = __ldg(Lr + (j0 + u) * Z + r);
 #pragma unroll
                 for (int u = 0; u < 8; u++)
-                    if (j0 + u < nb) A[((j0 + u) * Z + r) * V + v] = x[u] + 0.0f;
+                    if (j0 + u < nb) {
+                        if (!isfinite(x[u])) atomicOr(cd->status, IN_NONFINITE);
+                        A[((j0 + u) * Z + r) * V + v] = x[u] + 0.0f;
+                    }
             }
             for (int b = 0; b < nnz; b++) {
                 if constexpr (sizeof(MsgT) == 2)

@@ -59,9 +59,13 @@ __global__ void __launch_bounds__(512) k_layered_nms(const CodeDev *__restrict__
         int q = 0;
         if (cw < a.n_cw) {
             if (a.llr_type == LDPC_LLR_I8) {
-                q = sat_i(static_cast<const int8_t *>(a.llr)[cw * N + n], a.msg_sat);
+                const int raw = static_cast<const int8_t *>(a.llr)[cw * N + n];
+                if (raw < -a.msg_sat || raw > a.msg_sat) atomicOr(cd->status, IN_I8_RANGE);
+                q = sat_i(raw, a.msg_sat);
             } else {
-                const float p = __fmul_rn(a.scale, static_cast<const float *>(a.llr)[cw * N + n]);
+                const float in = static_cast<const float *>(a.llr)[cw * N + n];
+                if (!isfinite(in)) atomicOr(cd->status, IN_NONFINITE);
+                const float p = __fmul_rn(a.scale, in);
                 const float rr = rintf(p);
                 q = rr > (float)a.msg_sat ? a.msg_sat : (rr < -(float)a.msg_sat ? -a.msg_sat : (int)rr);
             }
@@ -226,9 +230,13 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
             const int64_t i = k * N + j * Z + r;
             int q;
             if (a.llr_type == LDPC_LLR_I8) {
-                q = sat_i(static_cast<const int8_t *>(a.llr)[i], a.msg_sat);
+                const int raw = static_cast<const int8_t *>(a.llr)[i];
+                if (raw < -a.msg_sat || raw > a.msg_sat) atomicOr(cd->status, IN_I8_RANGE);
+                q = sat_i(raw, a.msg_sat);
             } else {
-                const float rr = rintf(__fmul_rn(a.scale, __ldg(static_cast<const float *>(a.llr) + i)));
+                const float in = __ldg(static_cast<const float *>(a.llr) + i);
+                if (!isfinite(in)) atomicOr(cd->status, IN_NONFINITE);
+                const float rr = rintf(__fmul_rn(a.scale, in));
                 q = rr > (float)a.msg_sat ? a.msg_sat : (rr < -(float)a.msg_sat ? -a.msg_sat : (int)rr);
             }
             A[j * Z + r] = (int8_t)q;

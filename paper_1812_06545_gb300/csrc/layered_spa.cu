@@ -1,0 +1,370 @@
+// Horizontal layered sum-product decoding with the decoder state on chip (Sec. II
+// "Algorithm 2" schedule with the sum-product check rule of Sec. I).
+//
+// A persistent grid of one CTA per SM.  Each CTA holds C codeword slots; a slot keeps its
+// posterior APP [N] (fp32) and its check-to-variable messages R [E] (fp32 or fp16) in
+// shared memory for the whole decode of one codeword.  Thread (c, r) owns check row r of
+// every block row (layer) of slot c.  The Z checks of a QC layer touch disjoint variables
+// (each block is one circulant), so the row threads of a slot update a layer at once and a
+// CTA barrier separates consecutive layers.  Per check (the arithmetic of the flooding slot
+// decoder, only the schedule differs):
+//   Q_k   = APP_n - R_k                                   over the check's edges
+//   R'_k  = prod_{other} sgn Q * min(X, phi( sum_{other} phi(clampX |Q|) ))
+//           (stored as fp16 when the messages are half precision)
+//   APP_n = Q_k + R'_k   with R'_k the stored value, so that the next Q = APP - R removes
+//                        exactly what was added
+// After every full iteration each slot's hard decisions are checked against all of its
+// checks; a slot that converged (early exit) or reached max_iter writes its outputs and
+// takes the next codeword from the global work counter.
+//
+// APP is never -0: the refill adds +0 to the channel value and Q + R' is -0 only when both
+// are -0, which cannot happen while APP is not -0 (then Q = APP - R is not -0).  The sign
+// bit therefore is the hard decision [APP < 0] and sgn(0) = +1, as the oracle reads it.
+#include "slot_common.cuh"
+
+namespace ldpc {
+
+struct LayeredSpaArgs {
+    const float *llr;
+    int64_t n_cw;
+    int C, strideA, strideR;  // slots per CTA; per-slot APP and R strides (elements)
+    int max_iter, early_exit;
+    float X;
+    uint8_t *bits;
+    int32_t *iters;
+    float *app_out;
+    unsigned long long *next;
+};
+
+template <typename MsgT>
+struct MsgIO;
+template <>
+struct MsgIO<float> {
+    // store the message; return the value as stored
+    static __device__ __forceinline__ float st(float *p, float x)
+    {
+        *p = x;
+        return x;
+    }
+    static __device__ __forceinline__ float ld(const float *p) { return *p; }
+};
+template <>
+struct MsgIO<__half> {
+    static __device__ __forceinline__ float st(__half *p, float x)
+    {
+        const __half h = __float2half_rn(x);
+        *p = h;
+        return __half2float(h);
+    }
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
+};
+
+// One check of row r in the layer whose blocks start at table entry `ent` (R of block k of
+// the layer at bZ + k*Z), computed from and written back to the slot's APP and R.
+template <int D, bool EXACT, typename MsgT>
+__device__ __forceinline__ void layer_check(int dc, const int32_t *__restrict__ ent, int bZ, float *A, MsgT *Rc, int r,
+                                            int Z, float X, float Xb)
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    float a[D];                     // phi(clampX |Q|) in base-2 units, carrying the sign bit of Q
+    int xo[D <= 8 ? D : 1];         // wrapped row position of the edge inside its block
+    uint32_t sg = 0;
+    if constexpr (D <= 8 && sizeof(MsgT) == 4) {
+        float q[D];
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            if (EXACT || k < dc) {
+                const int e = ent[k];
+                int x = r + (e >> 16);
+                x -= (x >= Z) ? Z : 0;
+                xo[k] = x;
+                q[k] = A[(e & 0xffff) + x] - MsgIO<MsgT>::ld(Rc + bZ + k * Z + x);
+                const uint32_t qs = __float_as_uint(q[k]) & kSign;
+                sg ^= qs;
+                a[k] = __uint_as_float(__float_as_uint(fminf(s_psi_in(fminf(fabsf(q[k]), X)), Xb)) | qs);
+            }
+        }
+        // exclusive sums from suffix and prefix sums (no cancellation)
+        float sf[D + 1];
+        sf[D] = 0.0f;
+#pragma unroll
+        for (int k = D - 1; k >= 0; k--) sf[k] = (EXACT || k < dc) ? sf[k + 1] + fabsf(a[k]) : 0.0f;
+        float pre = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            if (EXACT || k < dc) {
+                const float mag = fminf(s_phi_out(pre + sf[k + 1]), X);
+                pre += fabsf(a[k]);
+                const float out = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(a[k]) ^ sg) & kSign));
+                const float rn = MsgIO<MsgT>::st(Rc + bZ + k * Z + xo[k], out);
+                A[(ent[k] & 0xffff) + xo[k]] = q[k] + rn;
+            }
+        }
+    } else {
+        // fewer live registers: Q is not held per edge but formed again from APP and R
+        // (neither is written before its own edge is), and above degree 8 neither is the
+        // wrapped position; exclusive sums as S - a_k, except for an edge holding more than
+        // half of S (at most one), whose sum of the others is formed directly
+        constexpr bool kHoldX = D <= 8;
+        float S = 0.0f, amax = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            if (EXACT || k < dc) {
+                const int e = ent[k];
+                int x = r + (e >> 16);
+                x -= (x >= Z) ? Z : 0;
+                if constexpr (kHoldX) xo[k] = x;
+                const float q = A[(e & 0xffff) + x] - MsgIO<MsgT>::ld(Rc + bZ + k * Z + x);
+                const uint32_t qs = __float_as_uint(q) & kSign;
+                sg ^= qs;
+                const float m = fminf(s_psi_in(fminf(fabsf(q), X)), Xb);
+                a[k] = __uint_as_float(__float_as_uint(m) | qs);
+                S += m;
+                amax = fmaxf(amax, m);
+            }
+        }
+        float o = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; k++)
+            if (EXACT || k < dc) o += (fabsf(a[k]) == amax) ? 0.0f : fabsf(a[k]);
+        const float sx = (amax > 0.5f * S) ? o : S - amax;
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            if (EXACT || k < dc) {
+                const float ak = fabsf(a[k]);
+                const float mag = fminf(s_phi_out(ak == amax ? sx : S - ak), X);
+                const float out = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(a[k]) ^ sg) & kSign));
+                const int e = ent[k];
+                int x;
+                if constexpr (kHoldX) {
+                    x = xo[k];
+                } else {
+                    x = r + (e >> 16);
+                    x -= (x >= Z) ? Z : 0;
+                }
+                MsgT *rp = Rc + bZ + k * Z + x;
+                float *ap = A + (e & 0xffff) + x;
+                const float q = *ap - MsgIO<MsgT>::ld(rp);
+                *ap = q + MsgIO<MsgT>::st(rp, out);
+            }
+        }
+    }
+}
+
+template <int D, int DMAX, typename MsgT>
+__device__ __forceinline__ void layer_check_dispatch(int dc, const int32_t *__restrict__ ent, int bZ, float *A,
+                                                     MsgT *Rc, int r, int Z, float X, float Xb)
+{
+    if constexpr (D >= DMAX) {
+        layer_check<DMAX, false, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb);
+    } else if constexpr (D <= 8) {
+        if (dc == D)
+            layer_check<D, true, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb);
+        else
+            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb);
+    } else {
+        if (dc <= D)
+            layer_check<D, false, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb);
+        else
+            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb);
+    }
+}
+
+// Threads per CTA for an instance: high-degree checks keep more values live per thread.
+// fp32 slots are limited to a few per CTA by shared memory, so their threads get more
+// registers; fp16 slots are twice as many and run the register-lean check form.
+template <int DMAX, typename MsgT>
+constexpr int lspa_threads_max()
+{
+    return sizeof(MsgT) == 4 ? (DMAX <= 16 ? 640 : 512) : (DMAX <= 8 ? 1024 : (DMAX <= 16 ? 768 : 512));
+}
+
+template <int DMAX, typename MsgT>
+__global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_spa(const CodeDev *__restrict__ cd,
+                                                                              const LayeredSpaArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int N = cd->N, Z = cd->Z, mb = cd->mb, nb = cd->nb, nnz = cd->nnz;
+    const int C = a.C;
+    int32_t *bad = reinterpret_cast<int32_t *>(smem);              // [SLOTS_MAX]
+    int64_t *fresh = reinterpret_cast<int64_t *>(bad + SLOTS_MAX);  // [SLOTS_MAX]
+    int32_t *t_ent = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);  // (s << 16) | j*Z per block
+    int32_t *t_rowptr = t_ent + nnz;
+    float *APPs = reinterpret_cast<float *>(smem + slots_smem_head(nnz + mb + 1));
+    MsgT *Rs = reinterpret_cast<MsgT *>(APPs + (size_t)C * a.strideA);
+
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const float X = a.X, Xb = a.X * kSLog2e;
+    for (int i = tid; i < nnz; i += nth) {
+        const int e = cd->ent[i];
+        t_ent[i] = ((e & 0xffff) << 16) | ((e >> 16) * Z);
+    }
+    for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
+    const int c = tid / Z, r = tid - (tid / Z) * Z;
+    const bool mine = c < C;
+    if (mine && r == 0) {
+        const unsigned long long k = atomicAdd(a.next, 1ull);
+        fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+        bad[c] = 0;
+    }
+    __syncthreads();
+    float *A = APPs + (size_t)(mine ? c : 0) * a.strideA;
+    MsgT *Rc = Rs + (size_t)(mine ? c : 0) * a.strideR;
+
+    // a slot given codeword k loads APP = L (+0: no -0 in APP) and clears its messages
+    auto refill = [&](int64_t k) {
+        const float *L = a.llr + k * N;
+        for (int j = 0; j < nb; j++) {
+            const float v = __ldg(L + j * Z + r);
+            if (!isfinite(v)) atomicOr(cd->status, IN_NONFINITE);
+            A[j * Z + r] = v + 0.0f;
+        }
+        for (int b = 0; b < nnz; b++) Rc[b * Z + r] = MsgT(0.0f);
+    };
+
+    int64_t cw = mine ? fresh[c] : -1;
+    int t = 0;
+    if (cw >= 0) refill(cw);
+    if (!__syncthreads_or(cw >= 0)) return;
+
+    for (;;) {
+        const bool busy = cw >= 0;
+        for (int l = 0; l < mb; l++) {
+            if (busy) {
+                const int b0 = t_rowptr[l];
+                layer_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ent + b0, b0 * Z, A, Rc, r, Z, X, Xb);
+            }
+            __syncthreads();
+        }
+        if (busy) t++;
+        // syndrome of the hard decisions (APP sign bits): row r of every layer
+        if (busy && a.early_exit) {
+            uint32_t par_any = 0;
+            for (int l = 0; l < mb; l++) {
+                uint32_t par = 0;
+                for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++) {
+                    const int e = t_ent[b];
+                    int x = r + (e >> 16);
+                    x -= (x >= Z) ? Z : 0;
+                    par ^= __float_as_uint(A[(e & 0xffff) + x]);
+                }
+                par_any |= par;
+            }
+            if (par_any & 0x80000000u) bad[c] = 1;
+        }
+        __syncthreads();
+        bool done = false;
+        if (busy) {
+            done = (a.early_exit && bad[c] == 0) || t >= a.max_iter;
+            if (done) {
+                uint8_t *Bo = a.bits + cw * N;
+                float *Ao = a.app_out ? a.app_out + cw * N : nullptr;
+                for (int j = 0; j < nb; j++) {
+                    const float v = A[j * Z + r];
+                    Bo[j * Z + r] = v < 0.0f ? 1 : 0;
+                    if (Ao) Ao[j * Z + r] = v;
+                }
+                if (r == 0) {
+                    a.iters[cw] = t;
+                    const unsigned long long k = atomicAdd(a.next, 1ull);
+                    fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+                }
+            }
+        }
+        __syncthreads();
+        if (busy) {
+            if (r == 0) bad[c] = 0;
+            if (done) {
+                cw = fresh[c];
+                t = 0;
+                if (cw >= 0) refill(cw);
+            }
+        }
+        if (!__syncthreads_or(cw >= 0)) break;
+    }
+}
+
+static size_t lspa_slot_bytes(const CodeDev &h, int msg)
+{
+    return (size_t)((h.N + 3) & ~3) * sizeof(float) +
+           (size_t)((h.E + 7) & ~7) * (msg == LDPC_MSG_F16 ? sizeof(__half) : sizeof(float));
+}
+
+static int lspa_threads_for(int dc_max, int msg)
+{
+    const int d = dc_max <= 8 ? 8 : dc_max <= 16 ? 16 : dc_max <= 24 ? 24 : 32;
+    if (msg == LDPC_MSG_F16)
+        return d == 8 ? lspa_threads_max<8, __half>() : d == 16 ? lspa_threads_max<16, __half>()
+                                                               : lspa_threads_max<32, __half>();
+    return d <= 16 ? lspa_threads_max<16, float>() : lspa_threads_max<32, float>();
+}
+
+static size_t lspa_smem(const CodeDev &h, int msg, int C)
+{
+    return slots_smem_head(h.nnz + h.mb + 1) + (size_t)C * lspa_slot_bytes(h, msg);
+}
+
+int layered_spa_slots_per_cta(const CodeDev &h, int msg)
+{
+    if (h.dc_max > 32 || h.N >= 65536) return 0;
+    int C = lspa_threads_for(h.dc_max, msg) / h.Z;
+    if (C > SLOTS_MAX) C = SLOTS_MAX;
+    int dev = 0, lim = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t limit = lim > 0 ? (size_t)lim : 227 * 1024;
+    while (C > 0 && lspa_smem(h, msg, C) > limit) C--;
+    return C;
+}
+
+template <int DMAX, typename MsgT>
+static cudaError_t launch_lspa(const CodeDev &h, const CodeDev *d, const LayeredSpaArgs &a, int msg, cudaStream_t s)
+{
+    const size_t sm = lspa_smem(h, msg, a.C);
+    cudaError_t e = ensure_smem<k_layered_spa<DMAX, MsgT>>(sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t ctas = nsm;
+    const int64_t need = (a.n_cw + a.C - 1) / a.C;
+    if (need < ctas) ctas = need;
+    const int threads = ((a.C * h.Z + 31) / 32) * 32;
+    LaunchScope ls(F_LAYERED_SPA, s);
+    k_layered_spa<DMAX, MsgT><<<(unsigned)ctas, threads, sm, s>>>(d, a);
+    return cudaGetLastError();
+}
+
+template <typename MsgT>
+static cudaError_t launch_lspa_d(const CodeDev &h, const CodeDev *d, const LayeredSpaArgs &a, int msg, cudaStream_t s)
+{
+    if (h.dc_max <= 8) return launch_lspa<8, MsgT>(h, d, a, msg, s);
+    if (h.dc_max <= 16) return launch_lspa<16, MsgT>(h, d, a, msg, s);
+    if (h.dc_max <= 24) return launch_lspa<24, MsgT>(h, d, a, msg, s);
+    return launch_lspa<32, MsgT>(h, d, a, msg, s);
+}
+
+cudaError_t layered_spa_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p, const float *llr,
+                               int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out, void *counter,
+                               cudaStream_t s)
+{
+    LayeredSpaArgs a;
+    a.llr = llr;
+    a.n_cw = n_cw;
+    a.C = layered_spa_slots_per_cta(h, p.msg);
+    if (a.C < 1) return cudaErrorInvalidValue;
+    a.strideA = (h.N + 3) & ~3;
+    a.strideR = (h.E + 7) & ~7;
+    a.max_iter = p.max_iter;
+    a.early_exit = p.early_exit;
+    a.X = p.phi_clamp;
+    a.bits = bits;
+    a.iters = iters;
+    a.app_out = app_out;
+    a.next = static_cast<unsigned long long *>(counter);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    return p.msg == LDPC_MSG_F16 ? launch_lspa_d<__half>(h, d, a, p.msg, s) : launch_lspa_d<float>(h, d, a, p.msg, s);
+}
+
+}  // namespace ldpc

@@ -100,6 +100,36 @@ LaunchScope::~LaunchScope()
     if (g_pending.size() > 4096) drain_pending();
 }
 
+// One input status word per device, allocated with the first code created on it and kept
+// for the life of the process (codes embed its address in their device tables).
+namespace {
+std::mutex g_status_mu;
+unsigned int *g_status[64];
+}  // namespace
+
+cudaError_t device_status_word(int dev, unsigned int **out)
+{
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (!g_status[dev]) {
+        unsigned int *w = nullptr;  // [0] the status word, [1] the value last taken from it
+        cudaError_t e = cudaMalloc(&w, 2 * sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemset(w, 0, 2 * sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            if (w) cudaFree(w);
+            return e;
+        }
+        g_status[dev] = w;
+    }
+    *out = g_status[dev];
+    return cudaSuccess;
+}
+
+// Swap the status word for zero in stream order (kernels of other streams may set bits at
+// any time; an exchange loses none of them).
+__global__ void k_take_status(unsigned int *w) { w[1] = atomicExch(w, 0u); }
+
 }  // namespace ldpc
 
 using ldpc::CodeDev;
@@ -189,6 +219,7 @@ ldpc_status ldpc_code_create(const int32_t *base, int32_t mb, int32_t nb, int32_
     h.K = h.N - h.M;
     h.E = nnz * Z;
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = ldpc::device_status_word(c->device, &h.status);
     if (e == cudaSuccess) e = cudaMalloc(&c->dev, sizeof(CodeDev));
     if (e == cudaSuccess) e = cudaMemcpy(c->dev, &h, sizeof(CodeDev), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -236,6 +267,18 @@ static ldpc_status check_params(const ldpc_code *c, const ldpc_decode_params *p,
         if (c->host.dc_max > 32) return fail(LDPC_ENOTSUP, "check degree %d > 32", c->host.dc_max);
         return LDPC_OK;
     }
+    if (p->sched == LDPC_SCHED_LAYERED && p->algo == LDPC_ALGO_SPA) {
+        if (p->msg != LDPC_MSG_F32 && p->msg != LDPC_MSG_F16)
+            return fail(LDPC_ENOTSUP, "layered SPA stores messages as F32 or F16");
+        if (!(p->phi_clamp > 1.0f) || !(p->phi_clamp <= 87.0f))
+            return fail(LDPC_EINVAL, "phi_clamp must be in (1, 87] so that phi(X) is a normal fp32 value");
+        if (llr_type != LDPC_LLR_F32) return fail(LDPC_EINVAL, "layered SPA takes fp32 LLRs");
+        if (p->impl != LDPC_IMPL_AUTO) return fail(LDPC_ENOTSUP, "layered SPA has only the on-chip slot decoder");
+        if (ldpc::layered_spa_slots_per_cta(c->host, p->msg) < 1)
+            return fail(LDPC_ENOTSUP, "code too large for on-chip layered SPA (N=%d, E=%d, dc_max=%d)", c->host.N,
+                        c->host.E, c->host.dc_max);
+        return LDPC_OK;
+    }
     if (p->sched == LDPC_SCHED_LAYERED && p->algo == LDPC_ALGO_NMS) {
         if (p->msg != LDPC_MSG_I8) return fail(LDPC_ENOTSUP, "layered min-sum stores I8 messages");
         if (p->impl == LDPC_IMPL_PLAIN) return fail(LDPC_ENOTSUP, "no plain layered implementation");
@@ -267,14 +310,21 @@ static bool use_slots(const ldpc_code *c, const ldpc_decode_params *p)
 // LDPC_IMPL_STREAMING asks for the one-CTA-per-group kernel, which needs no workspace.
 static bool use_layered_slots(const ldpc_code *c, const ldpc_decode_params *p)
 {
-    return p->sched == LDPC_SCHED_LAYERED && p->impl == LDPC_IMPL_AUTO && ldpc::layered_slots_per_cta(c->host) > 0 &&
-           c->tuned_layered != SCHED_STREAMING;
+    return p->sched == LDPC_SCHED_LAYERED && p->algo == LDPC_ALGO_NMS && p->impl == LDPC_IMPL_AUTO &&
+           ldpc::layered_slots_per_cta(c->host) > 0 && c->tuned_layered != SCHED_STREAMING;
+}
+
+// The layered sum-product always runs as persistent slots (check_params admits only codes
+// whose slot fits a CTA).
+static bool use_layered_spa(const ldpc_decode_params *p)
+{
+    return p->sched == LDPC_SCHED_LAYERED && p->algo == LDPC_ALGO_SPA;
 }
 
 static size_t ws_bytes(const ldpc_code *c, const ldpc_decode_params *p, int64_t n_cw)
 {
     if (n_cw == 0) return 0;
-    if (use_layered_slots(c, p)) return ldpc::SLOTS_WS_BYTES;
+    if (use_layered_slots(c, p) || use_layered_spa(p)) return ldpc::SLOTS_WS_BYTES;
     if (p->sched == LDPC_SCHED_LAYERED) return 0;
     if (use_slots(c, p)) return ldpc::SLOTS_WS_BYTES;
     return ldpc::flood_ws_layout(c->host, n_cw, p->msg, nullptr, nullptr);
@@ -283,7 +333,8 @@ static size_t ws_bytes(const ldpc_code *c, const ldpc_decode_params *p, int64_t 
 ldpc_status ldpc_workspace_size(const ldpc_code *c, const ldpc_decode_params *p, int64_t n_cw, size_t *bytes)
 {
     if (!bytes) return fail(LDPC_EINVAL, "bytes is NULL");
-    ldpc_status st = check_params(c, p, p && p->sched == LDPC_SCHED_LAYERED ? LDPC_LLR_I8 : LDPC_LLR_F32);
+    ldpc_status st =
+        check_params(c, p, p && p->sched == LDPC_SCHED_LAYERED && p->algo == LDPC_ALGO_NMS ? LDPC_LLR_I8 : LDPC_LLR_F32);
     if (st != LDPC_OK) return st;
     if (n_cw < 0) return fail(LDPC_EINVAL, "n_cw < 0");
     *bytes = ws_bytes(c, p, n_cw);
@@ -301,7 +352,7 @@ ldpc_status ldpc_decode_batch(const ldpc_code *c, const ldpc_decode_params *p, c
     if (!llr || !bits || !iters) return fail(LDPC_EINVAL, "llr, bits and iters must be non-NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e;
-    if (p->sched == LDPC_SCHED_LAYERED && !use_layered_slots(c, p)) {
+    if (p->sched == LDPC_SCHED_LAYERED && p->algo == LDPC_ALGO_NMS && !use_layered_slots(c, p)) {
         e = ldpc::layered_decode(c->host, c->dev, *p, llr, llr_type, n_cw, bits, iters, app, s);
         return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "layered decode launch");
     }
@@ -320,7 +371,10 @@ ldpc_status ldpc_decode_batch(const ldpc_code *c, const ldpc_decode_params *p, c
         }
         own = true;
     }
-    if (use_layered_slots(c, p)) {
+    if (use_layered_spa(p)) {
+        e = ldpc::layered_spa_decode(c->host, c->dev, *p, static_cast<const float *>(llr), n_cw, bits, iters, app, ws,
+                                     s);
+    } else if (use_layered_slots(c, p)) {
         e = ldpc::layered_slots_decode(c->host, c->dev, *p, llr, llr_type, n_cw, bits, iters, app, ws, s);
     } else if (use_slots(c, p)) {
         const ldpc::HostReq rq = {c, llr, n_cw, bits, iters, app};
@@ -354,7 +408,9 @@ ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldp
         if (q.n_cw < 0 || q.n_cw > ((int64_t)1 << 31)) return fail(LDPC_EINVAL, "request %d: bad n_cw", i);
         if (q.n_cw > 0 && (!q.llr_dev || !q.bits_dev || !q.iters_dev))
             return fail(LDPC_EINVAL, "request %d: llr, bits and iters must be non-NULL", i);
-        const bool fits = p->sched == LDPC_SCHED_FLOODING ? use_slots(q.code, p) : use_layered_slots(q.code, p);
+        const bool fits = p->sched == LDPC_SCHED_FLOODING ? use_slots(q.code, p)
+                          : use_layered_spa(p)               ? true
+                                                             : use_layered_slots(q.code, p);
         if (!fits) return fail(LDPC_ENOTSUP, "request %d: code too large for the slot decoders", i);
         int g = 0;
         while (g < ncodes && seen[g] != q.code) g++;
@@ -389,8 +445,12 @@ ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldp
         e = cudaSuccess;
         for (int i = 0; i < n_req && e == cudaSuccess; i++)
             if (hr[i].n_cw > 0)
-                e = ldpc::layered_slots_decode(hr[i].code->host, hr[i].code->dev, *p, hr[i].llr, llr_type,
-                                               hr[i].n_cw, hr[i].bits, hr[i].iters, hr[i].app, ws, s);
+                e = use_layered_spa(p)
+                        ? ldpc::layered_spa_decode(hr[i].code->host, hr[i].code->dev, *p,
+                                                   static_cast<const float *>(hr[i].llr), hr[i].n_cw, hr[i].bits,
+                                                   hr[i].iters, hr[i].app, ws, s)
+                        : ldpc::layered_slots_decode(hr[i].code->host, hr[i].code->dev, *p, hr[i].llr, llr_type,
+                                                     hr[i].n_cw, hr[i].bits, hr[i].iters, hr[i].app, ws, s);
     }
     if (own) {
         cudaError_t e2 = cudaFreeAsync(ws, s);
@@ -405,6 +465,7 @@ ldpc_status ldpc_autotune(ldpc_code *c, const ldpc_decode_params *p, const void 
     if (p && p->impl != LDPC_IMPL_AUTO) return fail(LDPC_EINVAL, "autotuning chooses the AUTO schedule (impl AUTO)");
     ldpc_status st = check_params(c, p, llr_type);
     if (st != LDPC_OK) return st;
+    if (use_layered_spa(p)) return fail(LDPC_ENOTSUP, "layered SPA has a single schedule: nothing to tune");
     if (n_cw < 1 || !llr) return fail(LDPC_EINVAL, "autotuning needs a non-empty sample of LLRs");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int *slot = p->sched == LDPC_SCHED_FLOODING ? &c->tuned_flood[p->msg == LDPC_MSG_F16 ? 1 : 0] : &c->tuned_layered;
@@ -466,6 +527,29 @@ ldpc_status ldpc_autotune(ldpc_code *c, const ldpc_decode_params *p, const void 
     cudaFree(ws);
     if (st != LDPC_OK) return st;
     return e == cudaSuccess ? LDPC_OK : cuda_fail(e, "autotune");
+}
+
+ldpc_status ldpc_stream_check(void *stream, uint32_t *flags)
+{
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    unsigned int *w = nullptr;
+    if (e == cudaSuccess) e = ldpc::device_status_word(dev, &w);
+    unsigned int v = 0;
+    if (e == cudaSuccess) {
+        ldpc::k_take_status<<<1, 1, 0, s>>>(w);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&v, w + 1, sizeof v, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream check");
+    if (flags) *flags = v;
+    if (v)
+        return fail(LDPC_EINVAL, "decoded input held %s%s%s", (v & ldpc::IN_NONFINITE) ? "non-finite fp32 LLRs" : "",
+                    (v & ldpc::IN_NONFINITE) && (v & ldpc::IN_I8_RANGE) ? " and " : "",
+                    (v & ldpc::IN_I8_RANGE) ? "int8 LLRs outside [-msg_sat, msg_sat]" : "");
+    return LDPC_OK;
 }
 
 ldpc_status ldpc_multi_workspace_size(size_t *bytes)

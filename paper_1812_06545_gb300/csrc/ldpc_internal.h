@@ -29,11 +29,16 @@ struct CodeDev {
     int32_t ent[NNZ_MAX];        // (j << 16) | s for block b
     int32_t colptr[NB_MAX + 1];  // entries of block column j: [colptr[j], colptr[j+1])
     int32_t colent[NNZ_MAX];     // (b << 16) | s for those blocks
+    unsigned int *status;        // the device's input status word (library-owned, one per device)
 };
+
+// Bits of the input status word: kernels that load channel LLRs set them (atomicOr, only
+// when an offending value is seen); ldpc_stream_check reads and clears the word.
+enum InputFlag : unsigned int { IN_NONFINITE = 1u, IN_I8_RANGE = 2u };
 
 // Per-kernel-family timing and launch accounting (see ldpc_profile_* in ldpc.h).
 enum Family { F_INTERLEAVE = 0, F_CN = 1, F_VN = 2, F_DEINTERLEAVE = 3, F_LAYERED = 4, F_PLAIN_CN = 5,
-              F_PLAIN_VN = 6, F_SLOTS = 7, F_COUNT = 8 };
+              F_PLAIN_VN = 6, F_SLOTS = 7, F_LAYERED_SPA = 8, F_COUNT = 9 };
 struct LaunchScope {
     LaunchScope(int family, cudaStream_t s);
     ~LaunchScope();
@@ -112,6 +117,12 @@ __host__ __device__ inline size_t slots_smem_head(int tbl_ints)
     return ((size_t)SLOTS_MAX * 16 + 16 + (size_t)tbl_ints * 4 + 15) & ~(size_t)15;
 }
 
+// Layered sum-product slot decoder (layered_spa.cu): slots per CTA (0: code too large).
+int layered_spa_slots_per_cta(const CodeDev &host, int msg);
+cudaError_t layered_spa_decode(const CodeDev &host, const CodeDev *dev, const ldpc_decode_params &p, const float *llr,
+                               int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out, void *counter,
+                               cudaStream_t s);
+
 // Flooding SPA slot decoder: supported when one codeword of the code fits a CTA.
 int slots_supported(const CodeDev &host, int msg);
 int slots_pairable(const CodeDev &host, int msg);
@@ -120,6 +131,9 @@ cudaError_t flood_multi_decode(const HostReq *reqs, int n, const ldpc_decode_par
 
 // Record a message for ldpc_last_error() on the calling thread.
 void set_error(const char *msg);
+
+// The device's input status word (allocated on first use; see InputFlag).
+cudaError_t device_status_word(int dev, unsigned int **out);
 
 }  // namespace ldpc
 

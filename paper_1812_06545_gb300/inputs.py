@@ -122,6 +122,14 @@ CODE_SPECS = {
     "qc12x24_z81_s2": (12, 24, 81, 2),     # rate 1/2, N = 1944
     "qc4x24_z81_s3": (4, 24, 81, 3),       # rate 5/6, N = 1944
     "qc34x68_z384_s5": (34, 68, 384, 5),   # rate 1/2, N = 26112 (large code)
+    # rate-1/2 codes at the frame lengths of the paper's throughput figures (Sec. IV:
+    # 576 .. 8000 bits; 1944 is qc12x24_z81_s2 above)
+    "qc12x24_z24_s6": (12, 24, 24, 6),     # N = 576
+    "qc16x32_z32_s7": (16, 32, 32, 7),     # N = 1024
+    "qc12x24_z50_s8": (12, 24, 50, 8),     # N = 1200
+    "qc12x24_z96_s9": (12, 24, 96, 9),     # N = 2304
+    "qc10x20_z200_s10": (10, 20, 200, 10),  # N = 4000
+    "qc20x40_z200_s11": (20, 40, 200, 11),  # N = 8000
 }
 # Mixed-code family: Z in {27, 54, 81} x rate {1/2, 2/3, 3/4, 5/6}, seeds 40 + i.
 for _i, (_Z, _mb) in enumerate([(z, m) for z in (27, 54, 81) for m in (12, 8, 6, 4)]):

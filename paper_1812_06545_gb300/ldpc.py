@@ -24,7 +24,7 @@ LDPC_MSG_F32, LDPC_MSG_F16, LDPC_MSG_I8 = 0, 1, 2
 LDPC_LLR_F32, LDPC_LLR_I8 = 0, 1
 LDPC_IMPL_AUTO, LDPC_IMPL_PLAIN, LDPC_IMPL_STREAMING = 0, 1, 2
 FAMILIES = {"interleave": 0, "check_node": 1, "variable_node": 2, "deinterleave": 3, "layered": 4,
-            "plain_check_node": 5, "plain_variable_node": 6, "slots": 7}
+            "plain_check_node": 5, "plain_variable_node": 6, "slots": 7, "layered_spa": 8}
 
 
 class LdpcError(RuntimeError):
@@ -91,6 +91,7 @@ def lib():
             "ldpc_session_pause": [vp, i32],
             "ldpc_session_stats_get": [vp, vp],
             "ldpc_sfu_throughput": [vp, vp, vp],
+            "ldpc_stream_check": [vp, vp],
             "ldpc_profile_enable": [i32],
             "ldpc_profile_read": [i32, vp, vp],
             "ldpc_profile_reset": [],
@@ -290,6 +291,23 @@ def ldpc_decode_host(handle: int, params: DecodeParams, llr_host, n_cw: int, bit
                                   _ptr(iters_host), int(n_streams), int(chunk_cw)), "ldpc_decode_host")
 
 
+def ldpc_stream_check(stream=None) -> int:
+    """Take the device's input status word after the work queued on ``stream``; returns the
+    flag bits (raises LdpcError with LDPC_EINVAL when a bit was set)."""
+    f = C.c_uint32()
+    _check(lib().ldpc_stream_check(_stream(stream), C.byref(f)), "ldpc_stream_check")
+    return f.value
+
+
+def ldpc_stream_flags(stream=None) -> int:
+    """Like ldpc_stream_check, but returns the flag bits instead of raising on them."""
+    f = C.c_uint32()
+    st = lib().ldpc_stream_check(_stream(stream), C.byref(f))
+    if st not in (LDPC_OK, LDPC_EINVAL):
+        _check(st, "ldpc_stream_check")
+    return f.value
+
+
 def ldpc_release_host_buffers() -> None:
     lib().ldpc_release_host_buffers()
 
@@ -346,6 +364,8 @@ FORMS = {
     "plain_f32": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F32, impl=LDPC_IMPL_PLAIN),
     "stream_f32": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F32, impl=LDPC_IMPL_STREAMING),
     "stream_f16": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F16, impl=LDPC_IMPL_STREAMING),
+    "layered_f32": dict(sched=LDPC_SCHED_LAYERED, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F32),
+    "layered_f16": dict(sched=LDPC_SCHED_LAYERED, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F16),
     "layered_i8": dict(sched=LDPC_SCHED_LAYERED, algo=LDPC_ALGO_NMS, msg=LDPC_MSG_I8),
     "layered_i8_group": dict(sched=LDPC_SCHED_LAYERED, algo=LDPC_ALGO_NMS, msg=LDPC_MSG_I8,
                              impl=LDPC_IMPL_STREAMING),
