@@ -442,6 +442,21 @@ def run_equal_fer(ldpc, dev, n_frames: int = 400000, chunk: int = 50000):
             best["form"] = form
             best["fer_within_10pct"] = bool(best["fer"] <= 1.1 * ref["fer"])
             best["ratio_vs_plain_f32"] = best["info_gbps"] / ref["info_gbps"]
+            if not best["fer_within_10pct"]:
+                # context for a form that cannot match the comparator's FER at E*: the Eb/N0 at
+                # which it reaches FER 1e-3 itself (max_iter as on the ladder's last rung)
+                eb2, prev = e_star, (e_star, best["fer"])
+                while eb2 < e_star + 2.0:
+                    eb2 += 0.1
+                    r2 = measure(code, pool, rate, form, eb2, best["max_iter"], n_frames // 4, 3000)
+                    if r2["fer"] <= 1e-3:
+                        f0, f1 = max(prev[1], 1e-9), max(r2["fer"], 1e-9)
+                        own = prev[0] + (np.log(1e-3) - np.log(f0)) / (np.log(f1) - np.log(f0)) * (eb2 - prev[0]) \
+                            if f1 < f0 else eb2
+                        best["own_ebn0_star_db"] = float(own)
+                        best["snr_gap_db"] = float(own - e_star)
+                        break
+                    prev = (eb2, r2["fer"])
             rows.append(best)
         out.append({"code": name, "N": code.N, "K": code.K, "ebn0_star_db": float(e_star),
                     "sweep_fp32_flooding": [{"ebn0_db": e, "fer": f} for e, f in pts], "reference": ref,
@@ -631,6 +646,17 @@ def main():
                                 f"1 / (2/ex2 + 2/lg2) edge updates per second"),
                 "traffic": traffic, "launches": n_sl, "avg_launch_ms": sl_ms / max(n_sl, 1),
                 "algorithmic_work": "edge updates = E x iterations run, summed over codewords"}
+    # the same throughput against the HBM limit of a flooding decoder that streams its state
+    # through HBM (R read and written, APP and L once per phase: 12E + 12N bytes per
+    # codeword-iteration at FP32): how close the on-chip design runs to that design's ceiling
+    cw_it_s = edge_updates / E / (sl_ms * 1e-3) if sl_ms > 0 else None
+    hbm_limit = hbm_peak * 1e9 / (12 * E + 12 * N)
+    roofline["streaming_hbm_equivalent"] = {
+        "codeword_iterations_per_s": cw_it_s, "hbm_bound_limit_per_s": hbm_limit,
+        "frac": (cw_it_s / hbm_limit) if cw_it_s else None,
+        "what": "codeword-iterations/s of the slot decoder over the HBM-bound limit of the streaming flooding "
+                "design (12E + 12N bytes per codeword-iteration at the measured copy bandwidth); the slot "
+                "decoder itself moves only the LLRs and decisions"}
 
     line = {"metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,

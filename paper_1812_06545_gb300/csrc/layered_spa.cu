@@ -3,17 +3,21 @@
 //
 // A persistent grid of one CTA per SM.  Each CTA holds C codeword slots; a slot keeps its
 // posterior APP [N] (fp32) and its check-to-variable messages R [E] (fp32 or fp16) in
-// shared memory for the whole decode of one codeword.  Thread (c, r) owns check row r of
-// every block row (layer) of slot c.  The Z checks of a QC layer touch disjoint variables
-// (each block is one circulant), so the row threads of a slot update a layer at once and a
-// CTA barrier separates consecutive layers.  Per check (the arithmetic of the flooding slot
-// decoder, only the schedule differs):
+// shared memory for the whole decode of one codeword.  A slot owns whole warps
+// (ceil(Z/32) of them) and thread r of the slot owns check row r of every block row
+// (layer).  The Z checks of a QC layer touch disjoint variables (each block is one
+// circulant), so the row threads update a layer at once and the slot's own barrier (a
+// named barrier, or the warp itself when Z <= 32) separates consecutive layers: slots run
+// independently, each at its own codeword and iteration, with no CTA-wide lock-step.
+// Messages are stored in check-row order, edge (b, r) at b*Z + r: the layered schedule has
+// no variable-node pass, so the row threads of a warp read and write them contiguously.
+// Per check (the arithmetic of the flooding slot decoder, only the schedule differs):
 //   Q_k   = APP_n - R_k                                   over the check's edges
 //   R'_k  = prod_{other} sgn Q * min(X, phi( sum_{other} phi(clampX |Q|) ))
 //           (stored as fp16 when the messages are half precision)
 //   APP_n = Q_k + R'_k   with R'_k the stored value, so that the next Q = APP - R removes
 //                        exactly what was added
-// After every full iteration each slot's hard decisions are checked against all of its
+// After every full iteration the slot's hard decisions are checked against all of its
 // checks; a slot that converged (early exit) or reached max_iter writes its outputs and
 // takes the next codeword from the global work counter.
 //
@@ -28,6 +32,7 @@ struct LayeredSpaArgs {
     const float *llr;
     int64_t n_cw;
     int C, strideA, strideR;  // slots per CTA; per-slot APP and R strides (elements)
+    int TPS;                  // threads per slot: whole warps covering Z rows
     int max_iter, early_exit;
     float X;
     uint8_t *bits;
@@ -60,14 +65,15 @@ struct MsgIO<__half> {
 };
 
 // One check of row r in the layer whose blocks start at table entry `ent` (R of block k of
-// the layer at bZ + k*Z), computed from and written back to the slot's APP and R.
+// the layer at bZ + k*Z + r), computed from and written back to the slot's APP and R.
 template <int D, bool EXACT, typename MsgT>
 __device__ __forceinline__ void layer_check(int dc, const int32_t *__restrict__ ent, int bZ, float *A, MsgT *Rc, int r,
                                             int Z, float X, float Xb)
 {
     constexpr uint32_t kSign = 0x80000000u;
+    MsgT *Rr = Rc + bZ + r;
     float a[D];                     // phi(clampX |Q|) in base-2 units, carrying the sign bit of Q
-    int xo[D <= 8 ? D : 1];         // wrapped row position of the edge inside its block
+    int ao[D <= 8 ? D : 1];         // APP index of the edge's variable
     uint32_t sg = 0;
     if constexpr (D <= 8 && sizeof(MsgT) == 4) {
         float q[D];
@@ -77,8 +83,8 @@ __device__ __forceinline__ void layer_check(int dc, const int32_t *__restrict__ 
                 const int e = ent[k];
                 int x = r + (e >> 16);
                 x -= (x >= Z) ? Z : 0;
-                xo[k] = x;
-                q[k] = A[(e & 0xffff) + x] - MsgIO<MsgT>::ld(Rc + bZ + k * Z + x);
+                ao[k] = (e & 0xffff) + x;
+                q[k] = A[ao[k]] - MsgIO<MsgT>::ld(Rr + k * Z);
                 const uint32_t qs = __float_as_uint(q[k]) & kSign;
                 sg ^= qs;
                 a[k] = __uint_as_float(__float_as_uint(fminf(s_psi_in(fminf(fabsf(q[k]), X)), Xb)) | qs);
@@ -96,16 +102,15 @@ __device__ __forceinline__ void layer_check(int dc, const int32_t *__restrict__ 
                 const float mag = fminf(s_phi_out(pre + sf[k + 1]), X);
                 pre += fabsf(a[k]);
                 const float out = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(a[k]) ^ sg) & kSign));
-                const float rn = MsgIO<MsgT>::st(Rc + bZ + k * Z + xo[k], out);
-                A[(ent[k] & 0xffff) + xo[k]] = q[k] + rn;
+                A[ao[k]] = q[k] + MsgIO<MsgT>::st(Rr + k * Z, out);
             }
         }
     } else {
         // fewer live registers: Q is not held per edge but formed again from APP and R
         // (neither is written before its own edge is), and above degree 8 neither is the
-        // wrapped position; exclusive sums as S - a_k, except for an edge holding more than
+        // variable's index; exclusive sums as S - a_k, except for an edge holding more than
         // half of S (at most one), whose sum of the others is formed directly
-        constexpr bool kHoldX = D <= 8;
+        constexpr bool kHoldIdx = D <= 8;
         float S = 0.0f, amax = 0.0f;
 #pragma unroll
         for (int k = 0; k < D; k++) {
@@ -113,8 +118,8 @@ __device__ __forceinline__ void layer_check(int dc, const int32_t *__restrict__ 
                 const int e = ent[k];
                 int x = r + (e >> 16);
                 x -= (x >= Z) ? Z : 0;
-                if constexpr (kHoldX) xo[k] = x;
-                const float q = A[(e & 0xffff) + x] - MsgIO<MsgT>::ld(Rc + bZ + k * Z + x);
+                if constexpr (kHoldIdx) ao[k] = (e & 0xffff) + x;
+                const float q = A[(e & 0xffff) + x] - MsgIO<MsgT>::ld(Rr + k * Z);
                 const uint32_t qs = __float_as_uint(q) & kSign;
                 sg ^= qs;
                 const float m = fminf(s_psi_in(fminf(fabsf(q), X)), Xb);
@@ -134,18 +139,17 @@ __device__ __forceinline__ void layer_check(int dc, const int32_t *__restrict__ 
                 const float ak = fabsf(a[k]);
                 const float mag = fminf(s_phi_out(ak == amax ? sx : S - ak), X);
                 const float out = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(a[k]) ^ sg) & kSign));
-                const int e = ent[k];
-                int x;
-                if constexpr (kHoldX) {
-                    x = xo[k];
+                int ai;
+                if constexpr (kHoldIdx) {
+                    ai = ao[k];
                 } else {
-                    x = r + (e >> 16);
+                    const int e = ent[k];
+                    int x = r + (e >> 16);
                     x -= (x >= Z) ? Z : 0;
+                    ai = (e & 0xffff) + x;
                 }
-                MsgT *rp = Rc + bZ + k * Z + x;
-                float *ap = A + (e & 0xffff) + x;
-                const float q = *ap - MsgIO<MsgT>::ld(rp);
-                *ap = q + MsgIO<MsgT>::st(rp, out);
+                const float q = A[ai] - MsgIO<MsgT>::ld(Rr + k * Z);
+                A[ai] = q + MsgIO<MsgT>::st(Rr + k * Z, out);
             }
         }
     }
@@ -172,22 +176,33 @@ __device__ __forceinline__ void layer_check_dispatch(int dc, const int32_t *__re
 
 // Threads per CTA for an instance: high-degree checks keep more values live per thread.
 // fp32 slots are limited to a few per CTA by shared memory, so their threads get more
-// registers; fp16 slots are twice as many and run the register-lean check form.
+// registers (672 = 7 slots of three warps at 96 registers); fp16 slots are twice as many
+// and run the register-lean check form.
 template <int DMAX, typename MsgT>
 constexpr int lspa_threads_max()
 {
-    return sizeof(MsgT) == 4 ? (DMAX <= 16 ? 640 : 512) : (DMAX <= 8 ? 1024 : (DMAX <= 16 ? 768 : 512));
+    return sizeof(MsgT) == 4 ? (DMAX <= 16 ? 672 : 512) : (DMAX <= 8 ? 1024 : (DMAX <= 16 ? 768 : 512));
+}
+
+// The barrier of one slot: its warps only (named barrier slot + 1; barrier 0 is the CTA's),
+// or nothing beyond the warp itself when the slot is one warp.
+__device__ __forceinline__ void slot_sync(int slot, int tps)
+{
+    if (tps == 32)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(slot + 1), "r"(tps) : "memory");
 }
 
 template <int DMAX, typename MsgT>
 __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_spa(const CodeDev *__restrict__ cd,
-                                                                              const LayeredSpaArgs a)
+                                                                                    const LayeredSpaArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = cd->N, Z = cd->Z, mb = cd->mb, nb = cd->nb, nnz = cd->nnz;
-    const int C = a.C;
-    int32_t *bad = reinterpret_cast<int32_t *>(smem);              // [SLOTS_MAX]
-    int64_t *fresh = reinterpret_cast<int64_t *>(bad + SLOTS_MAX);  // [SLOTS_MAX]
+    const int C = a.C, TPS = a.TPS;
+    int32_t *flag = reinterpret_cast<int32_t *>(smem);               // [SLOTS_MAX][2] unsatisfied check seen
+    int64_t *fresh = reinterpret_cast<int64_t *>(flag + 2 * SLOTS_MAX);  // [SLOTS_MAX] the slot's codeword
     int32_t *t_ent = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);  // (s << 16) | j*Z per block
     int32_t *t_rowptr = t_ent + nnz;
     float *APPs = reinterpret_cast<float *>(smem + slots_smem_head(nnz + mb + 1));
@@ -200,87 +215,81 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
         t_ent[i] = ((e & 0xffff) << 16) | ((e >> 16) * Z);
     }
     for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
-    const int c = tid / Z, r = tid - (tid / Z) * Z;
-    const bool mine = c < C;
-    if (mine && r == 0) {
-        const unsigned long long k = atomicAdd(a.next, 1ull);
-        fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
-        bad[c] = 0;
-    }
     __syncthreads();
-    float *A = APPs + (size_t)(mine ? c : 0) * a.strideA;
-    MsgT *Rc = Rs + (size_t)(mine ? c : 0) * a.strideR;
 
-    // a slot given codeword k loads APP = L (+0: no -0 in APP) and clears its messages
-    auto refill = [&](int64_t k) {
-        const float *L = a.llr + k * N;
-        for (int j = 0; j < nb; j++) {
-            const float v = __ldg(L + j * Z + r);
-            if (!isfinite(v)) atomicOr(cd->status, IN_NONFINITE);
-            A[j * Z + r] = v + 0.0f;
-        }
-        for (int b = 0; b < nnz; b++) Rc[b * Z + r] = MsgT(0.0f);
-    };
-
-    int64_t cw = mine ? fresh[c] : -1;
-    int t = 0;
-    if (cw >= 0) refill(cw);
-    if (!__syncthreads_or(cw >= 0)) return;
+    const int c = tid / TPS, r = tid - (tid / TPS) * TPS;
+    if (c >= C) return;  // whole warps beyond the last slot (none when blockDim = C * TPS)
+    const bool row = r < Z;
+    float *A = APPs + (size_t)c * a.strideA;
+    MsgT *Rc = Rs + (size_t)c * a.strideR;
 
     for (;;) {
-        const bool busy = cw >= 0;
-        for (int l = 0; l < mb; l++) {
-            if (busy) {
-                const int b0 = t_rowptr[l];
-                layer_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ent + b0, b0 * Z, A, Rc, r, Z, X, Xb);
-            }
-            __syncthreads();
+        if (r == 0) {
+            const unsigned long long k = atomicAdd(a.next, 1ull);
+            fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
         }
-        if (busy) t++;
-        // syndrome of the hard decisions (APP sign bits): row r of every layer
-        if (busy && a.early_exit) {
-            uint32_t par_any = 0;
+        slot_sync(c, TPS);  // also: every thread is done with the previous codeword
+        const int64_t cw = fresh[c];
+        if (cw < 0) break;
+        if (r == 0) flag[2 * c] = flag[2 * c + 1] = 0;
+        // load the codeword: APP = L (+0: no -0 in APP), messages cleared
+        if (row) {
+            const float *L = a.llr + cw * N;
+            for (int j = 0; j < nb; j++) {
+                const float v = __ldg(L + j * Z + r);
+                if (!isfinite(v)) atomicOr(cd->status, IN_NONFINITE);
+                A[j * Z + r] = v + 0.0f;
+            }
+            for (int b = 0; b < nnz; b++) Rc[b * Z + r] = MsgT(0.0f);
+        }
+        slot_sync(c, TPS);
+        int t = 0;
+        for (;;) {
             for (int l = 0; l < mb; l++) {
-                uint32_t par = 0;
-                for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++) {
-                    const int e = t_ent[b];
-                    int x = r + (e >> 16);
-                    x -= (x >= Z) ? Z : 0;
-                    par ^= __float_as_uint(A[(e & 0xffff) + x]);
+                if (row) {
+                    const int b0 = t_rowptr[l];
+                    layer_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ent + b0, b0 * Z, A, Rc, r, Z, X,
+                                                        Xb);
                 }
-                par_any |= par;
+                slot_sync(c, TPS);
             }
-            if (par_any & 0x80000000u) bad[c] = 1;
-        }
-        __syncthreads();
-        bool done = false;
-        if (busy) {
-            done = (a.early_exit && bad[c] == 0) || t >= a.max_iter;
-            if (done) {
-                uint8_t *Bo = a.bits + cw * N;
-                float *Ao = a.app_out ? a.app_out + cw * N : nullptr;
-                for (int j = 0; j < nb; j++) {
-                    const float v = A[j * Z + r];
-                    Bo[j * Z + r] = v < 0.0f ? 1 : 0;
-                    if (Ao) Ao[j * Z + r] = v;
+            t++;
+            // syndrome of the hard decisions (APP sign bits): row r of every layer; the
+            // iteration's flag alternates so that clearing the next one races with nothing
+            bool conv = false;
+            if (a.early_exit) {
+                if (row) {
+                    uint32_t par_any = 0;
+                    for (int l = 0; l < mb; l++) {
+                        uint32_t par = 0;
+                        for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++) {
+                            const int e = t_ent[b];
+                            int x = r + (e >> 16);
+                            x -= (x >= Z) ? Z : 0;
+                            par ^= __float_as_uint(A[(e & 0xffff) + x]);
+                        }
+                        par_any |= par;
+                    }
+                    if (par_any & 0x80000000u) flag[2 * c + (t & 1)] = 1;
                 }
-                if (r == 0) {
-                    a.iters[cw] = t;
-                    const unsigned long long k = atomicAdd(a.next, 1ull);
-                    fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
-                }
+                slot_sync(c, TPS);
+                conv = flag[2 * c + (t & 1)] == 0;
+                if (r == 0) flag[2 * c + ((t + 1) & 1)] = 0;
             }
+            if (conv || t >= a.max_iter) break;
         }
-        __syncthreads();
-        if (busy) {
-            if (r == 0) bad[c] = 0;
-            if (done) {
-                cw = fresh[c];
-                t = 0;
-                if (cw >= 0) refill(cw);
+        if (row) {
+            uint8_t *Bo = a.bits + cw * N;
+            float *Ao = a.app_out ? a.app_out + cw * N : nullptr;
+            for (int j = 0; j < nb; j++) {
+                const float v = A[j * Z + r];
+                Bo[j * Z + r] = v < 0.0f ? 1 : 0;
+                if (Ao) Ao[j * Z + r] = v;
             }
+            if (r == 0) a.iters[cw] = t;
         }
-        if (!__syncthreads_or(cw >= 0)) break;
+        // the next codeword is announced before the barrier at the top of the loop and the
+        // flags are cleared after it, when every thread has finished with this codeword
     }
 }
 
@@ -304,11 +313,15 @@ static size_t lspa_smem(const CodeDev &h, int msg, int C)
     return slots_smem_head(h.nnz + h.mb + 1) + (size_t)C * lspa_slot_bytes(h, msg);
 }
 
+static int lspa_tps(const CodeDev &h) { return ((h.Z + 31) / 32) * 32; }
+
 int layered_spa_slots_per_cta(const CodeDev &h, int msg)
 {
     if (h.dc_max > 32 || h.N >= 65536) return 0;
-    int C = lspa_threads_for(h.dc_max, msg) / h.Z;
+    const int tps = lspa_tps(h);
+    int C = lspa_threads_for(h.dc_max, msg) / tps;
     if (C > SLOTS_MAX) C = SLOTS_MAX;
+    if (tps > 32 && C > 15) C = 15;  // named barriers 1..15
     int dev = 0, lim = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -329,9 +342,8 @@ static cudaError_t launch_lspa(const CodeDev &h, const CodeDev *d, const Layered
     int64_t ctas = nsm;
     const int64_t need = (a.n_cw + a.C - 1) / a.C;
     if (need < ctas) ctas = need;
-    const int threads = ((a.C * h.Z + 31) / 32) * 32;
     LaunchScope ls(F_LAYERED_SPA, s);
-    k_layered_spa<DMAX, MsgT><<<(unsigned)ctas, threads, sm, s>>>(d, a);
+    k_layered_spa<DMAX, MsgT><<<(unsigned)ctas, a.C * a.TPS, sm, s>>>(d, a);
     return cudaGetLastError();
 }
 
@@ -353,6 +365,7 @@ cudaError_t layered_spa_decode(const CodeDev &h, const CodeDev *d, const ldpc_de
     a.n_cw = n_cw;
     a.C = layered_spa_slots_per_cta(h, p.msg);
     if (a.C < 1) return cudaErrorInvalidValue;
+    a.TPS = lspa_tps(h);
     a.strideA = (h.N + 3) & ~3;
     a.strideR = (h.E + 7) & ~7;
     a.max_iter = p.max_iter;
