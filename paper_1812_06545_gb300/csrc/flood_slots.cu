@@ -36,6 +36,11 @@
 
 namespace ldpc {
 
+// Per-slot strides of APP and R (elements): at least the length, and congruent to Z modulo
+// the 32 shared-memory banks, so that a warp whose rows run from the end of one slot group
+// into the start of the next sees the two groups' rows as one contiguous bank sequence.
+__host__ __device__ inline int slot_stride(int n, int Z) { return n + ((Z % 32) - (n % 32) + 32) % 32; }
+
 struct FloodMultiArgs {
     MultiDesc d;
     unsigned long long *next;  // [n_groups] work counters, zero at launch
@@ -69,8 +74,8 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
         const CodeDev *cd = gd.code;
         const int N = gd.N, Z = gd.Z, mb = gd.mb, nb = gd.nb, nnz = gd.nnz;
         const int C = gd.C, G = gd.C / V;
-        const int strideA = (N + 3) & ~3, strideR = (gd.E + 7) & ~7;
-        MsgT *Rs = reinterpret_cast<MsgT *>(APPs + (size_t)C * strideA);
+        const int strideA = slot_stride(N, Z), strideR = slot_stride(gd.E, Z);
+        MsgT *Rs = reinterpret_cast<MsgT *>(APPs + (((size_t)C * strideA + 3) & ~(size_t)3));
         int32_t *t_colent = t_ent + nnz;
         int32_t *t_rowptr = t_colent + nnz;
         int32_t *t_colptr = t_rowptr + mb + 1;
@@ -301,11 +306,11 @@ static size_t max_smem_optin()
 
 static int tables_ints(const CodeDev &h) { return 2 * h.nnz + h.mb + 1 + h.nb + 1; }
 
-static size_t slot_bytes(const CodeDev &h, int msg)
+// Shared memory of C slots of a code: the APP region (16-byte aligned end) and the messages.
+static size_t slots_bytes(const CodeDev &h, int msg, int C)
 {
-    const size_t sa = (size_t)((h.N + 3) & ~3) * sizeof(float);
-    const size_t sr = (size_t)((h.E + 7) & ~7) * (msg == LDPC_MSG_F16 ? sizeof(__half) : sizeof(float));
-    return sa + sr;
+    const size_t sa = ((size_t)C * slot_stride(h.N, h.Z) * sizeof(float) + 15) & ~(size_t)15;
+    return sa + (size_t)C * slot_stride(h.E, h.Z) * (msg == LDPC_MSG_F16 ? sizeof(__half) : sizeof(float));
 }
 
 // Slots of one code per CTA with V codewords per thread, given the table space reserved.
@@ -314,7 +319,7 @@ static int slots_for(const CodeDev &h, int msg, int V, int tbl_ints, size_t limi
     if (h.dc_max > 32 || h.N >= 65536) return 0;
     int C = (int)((V == 2 ? slot_threads_max<2>() : slot_threads_max<1>()) / h.Z) * V;
     if (C > SLOTS_MAX) C = SLOTS_MAX;
-    while (C > 0 && slots_smem_head(tbl_ints) + (size_t)C * slot_bytes(h, msg) > limit) C--;
+    while (C > 0 && slots_smem_head(tbl_ints) + slots_bytes(h, msg, C) > limit) C--;
     C -= C % V;
     return C;
 }
@@ -423,7 +428,7 @@ cudaError_t flood_multi_decode(const HostReq *reqs, int n, const ldpc_decode_par
         }
         gd.req_end = nr;
         gd.n_items = items;
-        const size_t sm = slots_smem_head(tbl) + (size_t)gd.C * slot_bytes(h, p.msg);
+        const size_t sm = slots_smem_head(tbl) + slots_bytes(h, p.msg, gd.C);
         smem = sm > smem ? sm : smem;
         const int th = ((gd.C / V * h.Z + 31) / 32) * 32;
         threads = th > threads ? th : threads;
