@@ -193,13 +193,15 @@ def oracle_sample_rate(frames, code_name: str, max_iter: int, budget_s: float, t
     n = int(max(8, min(len(frames[0][2]), budget_s / (per_cw * len(frames)))))
     t0 = time.perf_counter()
     errs = 0
+    obits = []
     for eb, c, L in frames:
         _, bits, _ = oc.spa_flood(L[:n], max_iter, True, nthreads=threads)
         errs += int((bits != c[:n]).any(axis=1).sum())
+        obits.append(bits)
     dt = time.perf_counter() - t0
     rate = n * len(frames) * oc.K / dt
     return rate, f"first {n} codewords of each of the {len(frames)} Eb/N0 batches ({n * len(frames)} codewords)", \
-        cores, errs, n * len(frames)
+        cores, errs, n * len(frames), obits
 
 
 # ------------------------------------------------------------------ serving loop
@@ -329,7 +331,8 @@ def run_paper_shape(ldpc, dev, reps: int = 3):
         chunk = (n + 11) // 12
         for form in ("layered_f32", "layered_i8"):
             for T in (5, 10):
-                p = ldpc.params_for(form, max_iter=T, early_exit=0)
+                kw = {"llr_scale": I.llr_scale_for(code.K / code.N, 2.0)} if form == "layered_i8" else {}
+                p = ldpc.params_for(form, max_iter=T, early_exit=0, **kw)
                 wsb = ldpc.ldpc_workspace_size(code.handle, p, n)
                 ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
                 times = []
@@ -385,7 +388,8 @@ def run_equal_fer(ldpc, dev, n_frames: int = 400000, chunk: int = 50000):
         return (2.0 / s2) * y, idx
 
     def measure(code, pool, rate, form, eb, max_iter, n, seed0):
-        p = ldpc.params_for(form, max_iter=max_iter, early_exit=1)
+        kw = {"llr_scale": I.llr_scale_for(rate, eb)} if form == "layered_i8" else {}
+        p = ldpc.params_for(form, max_iter=max_iter, early_exit=1, **kw)
         errs, ms, it_sum = 0, 0.0, 0
         for k in range(0, n, chunk):
             m = min(chunk, n - k)
@@ -512,6 +516,8 @@ def main():
         return run_reference(args)
 
     import torch
+
+    from paper_1812_06545_gb300 import inputs as I
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -671,6 +677,8 @@ def main():
             "avg_iterations": float(np.mean(np.concatenate(iters_np))), "fer": fer,
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
 
+    gpu_bits = {"flood_f32": [b.cpu().numpy() for b in bits]}
+
     # ---------------- other forms on the same inputs
     if not args.no_forms:
         forms = {}
@@ -682,6 +690,8 @@ def main():
             fms = max_over_ranks(fms)
             fv = units * code.K / (fms * 1e-3) / 1e9
             fi_np = [x.cpu().numpy() for x in fi]
+            if form == "flood_f16":
+                gpu_bits[form] = [b.cpu().numpy() for b in fb]
             ffer = {f"{eb:.2f}": float((b.cpu().numpy() != c).any(axis=1).mean()) for (eb, c, _), b in zip(frames, fb)}
             forms[form] = {"value": fv, "ms_per_step": fms / args.steps, "fer": ffer, "gpu_launches": fl,
                            "avg_iterations": float(np.mean(np.concatenate(fi_np)))}
@@ -698,11 +708,37 @@ def main():
         forms["flood_f32"] = {"value": value, "vs_plain_f32": value / plain}
         for f in ("flood_f16", "layered_f32", "layered_f16", "stream_f32", "stream_f16"):
             forms[f]["vs_plain_f32"] = forms[f]["value"] / plain
+        # the small latency case: 128 codewords of the N=648 code, 10 fixed iterations, the
+        # plain comparator beside the slot decoder (whole decode state L2-resident)
+        sw, SB, SZ, sframes = workload_frames("flood_n648_b128", rank)
+        scode = ldpc.Code(SB, SZ)
+        sx = torch.from_numpy(sframes[0][2]).to(dev)
+        small = {"workload": "flood_n648_b128 (128 codewords, N=648 rate 1/2, 2.0 dB, 10 fixed iterations)"}
+        for form in ("plain_f32", "flood_f32", "layered_f32"):
+            sp = ldpc.params_for(form, max_iter=sw.max_iter, early_exit=0)
+            sb = torch.empty((sw.batch, scode.N), dtype=torch.uint8, device=dev)
+            si = torch.empty((sw.batch,), dtype=torch.int32, device=dev)
+            swsb = ldpc.ldpc_workspace_size(scode.handle, sp, sw.batch)
+            sws = torch.empty(max(swsb, 256), dtype=torch.uint8, device=dev)
+            lat_us = []
+            for k in range(60):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ldpc.ldpc_decode_batch(scode.handle, sp, sx, ldpc.LDPC_LLR_F32, sw.batch, sb, si, None, sws, swsb,
+                                       stream)
+                e1.record(stream)
+                e1.synchronize()
+                if k >= 10:
+                    lat_us.append(e0.elapsed_time(e1) * 1e3)
+            small[form] = {"p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
+                           "info_gbps": sw.batch * scode.K / (np.percentile(lat_us, 50) * 1e-6) / 1e9}
+        forms["small_latency"] = small
         # int8 layered min-sum on its own workload (rate 5/6, 65536 codewords, 4.0 dB)
         lw, LB, LZ, lframes = workload_frames(LAYERED_WORKLOAD, rank)
         lcode = ldpc.Code(LB, LZ)
         lx = torch.from_numpy(lframes[0][2]).to(dev)        # fp32 LLRs; quantised inside the kernel
-        lp = ldpc.params_for("layered_i8", max_iter=lw.max_iter)
+        lp = ldpc.params_for("layered_i8", max_iter=lw.max_iter,
+                             llr_scale=I.llr_scale_for(lcode.K / lcode.N, lw.ebn0_db[0]))
         lbits = torch.empty((lw.batch, lcode.N), dtype=torch.uint8, device=dev)
         lit = torch.empty((lw.batch,), dtype=torch.int32, device=dev)
         for _ in range(args.warmup):
@@ -722,7 +758,6 @@ def main():
         lv = world * args.steps * lw.batch * lcode.K / (lms * 1e-3) / 1e9
         lit_np = lit.cpu().numpy()
         # mixed codes in one persistent launch: 20000 codewords over 12 codes (FP16 messages)
-        from paper_1812_06545_gb300 import inputs as I
 
         mixed = I.mixed_batch(20000, 40 + rank)
         mreqs, mouts, mK = [], [], 0
@@ -800,9 +835,24 @@ def main():
 
     # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, sample, cores, errs, nfr = oracle_sample_rate(frames, w.code, w.max_iter, args.cpu_seconds)
+        rate, sample, cores, errs, nfr, obits = oracle_sample_rate(frames, w.code, w.max_iter, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate / 1e9, "unit": "Gbit/s", "cores": cores, "kind": "oracle",
                                 "sample": sample, "fer_sample": errs / nfr}
+        # the flooding forms against the FP64 oracle on the same sampled codewords: FER delta
+        # per Eb/N0 point and the share of identical decisions
+        deltas = {}
+        for form, gb in gpu_bits.items():
+            per = {}
+            same = tot = 0
+            for (eb, c, _), ob, g in zip(frames, obits, gb):
+                n = ob.shape[0]
+                fo = float((ob != c[:n]).any(axis=1).mean())
+                fg = float((g[:n] != c[:n]).any(axis=1).mean())
+                per[f"{eb:.2f}"] = {"oracle_fer": fo, "gpu_fer": fg, "delta": fg - fo}
+                same += int((g[:n] == ob).all(axis=1).sum())
+                tot += n
+            deltas[form] = {"per_ebn0": per, "identical_decisions": same / tot}
+        line["cpu_baseline"]["fer_delta_vs_oracle"] = deltas
     if rank == 0:
         print(json.dumps(line))
     if dist:

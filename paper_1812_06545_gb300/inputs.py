@@ -273,6 +273,16 @@ def mixed_batch(n_total: int = 20000, seed: int = 40):
     return out
 
 
+def llr_scale_for(rate: float, ebn0_db: float, sat: int = 31) -> float:
+    """Quantiser scale s of the int8 layered min-sum (q = sat(rint(s L))): the power of two
+    nearest to sat / (4 E|L|), so that saturation sits at about four mean channel LLRs.
+    E|L| = 2/sigma^2 = 4 R Eb/N0 for BPSK/AWGN.  (A parameter choice, measured on the oracle:
+    on the rate-5/6 code at 4.0 dB, s = 1 / 2 / 4 give FER 0.002 / 0.0085 / 0.79; on the
+    rate-1/2 code at 2.5 dB, 0.16 / 0.0048 / 0.19.)"""
+    mean = 4.0 * rate * 10.0 ** (ebn0_db / 10.0)
+    return float(2.0 ** round(np.log2(sat / (4.0 * mean))))
+
+
 def make_frames(code: str, n: int, ebn0_db: float, info_seed: int, noise_seed: int):
     """Encode n random-info codewords of ``code`` and pass them through BPSK/AWGN.
 
