@@ -177,20 +177,22 @@ __global__ void __launch_bounds__(512) k_layered_nms(const CodeDev *__restrict__
 // ------------------------------------------------------------------ slot decoder
 
 // Persistent form: one CTA per SM holds C codeword slots (APP and R of each in shared
-// memory).  A slot owns whole warps (ceil(Z/32) of them); thread r of the slot owns check
-// row r of every layer, and the slot's own barrier (a named barrier, or the warp itself when
-// Z <= 32) separates its layers, so every slot runs independently at its own codeword and
-// iteration.  Messages are stored in check-row order, edge (b, r) at b*Z + r (contiguous for
-// the row threads; the layered schedule has no variable-node pass).  After every full
-// iteration the slot's hard decisions are checked against all of its checks; a slot that
-// converged (or reached max_iter) writes its outputs and takes the next codeword from the
-// global work counter.
+// memory), arranged in barrier groups of K slots.  A group's threads cover its K*Z check rows
+// packed into whole warps; thread u of a group owns row u mod Z of slot u / Z, for every
+// layer.  A group's own barrier (a named barrier, or the warp itself when the group is one
+// warp) separates its layers, so the slots of a group run in lock-step while the groups run
+// independently: K trades the idle lanes of a warp-aligned slot (Z not a multiple of 32)
+// against waiting for the slowest slot of a group.  Messages are stored in check-row order,
+// edge (b, r) at b*Z + r (contiguous for the row threads; the layered schedule has no
+// variable-node pass).  After every full iteration each slot's hard decisions are checked
+// against all of its checks; a slot that converged (or reached max_iter) writes its outputs
+// and takes the next codeword from the global work counter at the group's next iteration.
 struct LayeredSlotArgs {
     const void *llr;
     int llr_type;
     float scale;
     int64_t n_cw;
-    int C, TPS, strideA, strideR;
+    int C, K, TPG, strideA, strideR;  // slots, slots per group, threads per group, strides
     int max_iter, early_exit, alpha_num, alpha_shift, msg_sat, app_sat;
     uint8_t *bits;
     int32_t *iters;
@@ -198,14 +200,14 @@ struct LayeredSlotArgs {
     unsigned long long *next;
 };
 
-// The barrier of one slot: its warps only (named barrier slot + 1; barrier 0 is the CTA's),
-// or nothing beyond the warp itself when the slot is one warp.
-__device__ __forceinline__ void lslot_sync(int slot, int tps)
+// The barrier of one group: its warps only (named barrier group + 1; barrier 0 is the CTA's),
+// or nothing beyond the warp itself when the group is one warp.
+__device__ __forceinline__ void lgroup_sync(int grp, int tpg)
 {
-    if (tps == 32)
+    if (tpg == 32)
         __syncwarp();
     else
-        asm volatile("bar.sync %0, %1;" ::"r"(slot + 1), "r"(tps) : "memory");
+        asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(tpg) : "memory");
 }
 
 template <int DMAX>
@@ -213,10 +215,11 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = cd->N, Z = cd->Z, mb = cd->mb, nb = cd->nb, nnz = cd->nnz;
-    const int C = a.C, TPS = a.TPS;
-    int32_t *flag = reinterpret_cast<int32_t *>(smem);                  // [SLOTS_MAX][2]
-    int64_t *fresh = reinterpret_cast<int64_t *>(flag + 2 * SLOTS_MAX);  // [SLOTS_MAX]
-    int32_t *t_ent = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);     // (s << 16) | j*Z
+    const int C = a.C, K = a.K, TPG = a.TPG;
+    int32_t *bad = reinterpret_cast<int32_t *>(smem);                 // [SLOTS_MAX] unsatisfied check seen
+    int32_t *gany = bad + SLOTS_MAX;                                   // [SLOTS_MAX / 2][2] group vote
+    int64_t *fresh = reinterpret_cast<int64_t *>(gany + SLOTS_MAX);    // [SLOTS_MAX]
+    int32_t *t_ent = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);   // (s << 16) | j*Z
     int32_t *t_rowptr = t_ent + nnz;
     int8_t *APPs = reinterpret_cast<int8_t *>(smem + slots_smem_head(nnz + mb + 1));
     int8_t *Rs = APPs + (size_t)C * a.strideA;
@@ -227,121 +230,146 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
         t_ent[i] = ((e & 0xffff) << 16) | ((e >> 16) * Z);
     }
     for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
+    const int g = tid / TPG, u = tid - (tid / TPG) * TPG;
+    const int c = g * K + u / Z, r = u - (u / Z) * Z;
+    const bool mine = u < K * Z && c < C;  // a row of a slot (else an idle lane of the group)
+    if (tid == 0)
+        for (int i = 0; i < SLOTS_MAX; i++) gany[i] = 0;
+    if (mine && r == 0) {
+        const unsigned long long k = atomicAdd(a.next, 1ull);
+        fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+        bad[c] = 0;
+    }
     __syncthreads();
+    if (g * K >= C) return;  // whole warps beyond the last group
+    int8_t *A = APPs + (size_t)(mine ? c : 0) * a.strideA;
+    int8_t *Rc = Rs + (size_t)(mine ? c : 0) * a.strideR;
+    int ph = 0;
+    // OR of a predicate over the group (every thread of the group calls it at the same
+    // point; the vote alternates between two words so that clearing the next one races with
+    // nothing)
+    auto group_any = [&](bool pred) {
+        if (pred) gany[2 * g + ph] = 1;
+        lgroup_sync(g, TPG);
+        const bool any = gany[2 * g + ph] != 0;
+        if (u == 0) gany[2 * g + (ph ^ 1)] = 0;
+        ph ^= 1;
+        return any;
+    };
 
-    const int c = tid / TPS, r = tid - (tid / TPS) * TPS;
-    if (c >= C) return;  // whole warps beyond the last slot (none when blockDim = C * TPS)
-    const bool row = r < Z;
-    int8_t *A = APPs + (size_t)c * a.strideA;
-    int8_t *Rc = Rs + (size_t)c * a.strideR;
+    auto refill = [&](int64_t k) {
+        for (int j = 0; j < nb; j++) {
+            const int64_t i = k * N + j * Z + r;
+            int q;
+            if (a.llr_type == LDPC_LLR_I8) {
+                const int raw = static_cast<const int8_t *>(a.llr)[i];
+                if (raw < -a.msg_sat || raw > a.msg_sat) atomicOr(cd->status, IN_I8_RANGE);
+                q = sat_i(raw, a.msg_sat);
+            } else {
+                const float in = __ldg(static_cast<const float *>(a.llr) + i);
+                if (!isfinite(in)) atomicOr(cd->status, IN_NONFINITE);
+                const float rr = rintf(__fmul_rn(a.scale, in));
+                q = rr > (float)a.msg_sat ? a.msg_sat : (rr < -(float)a.msg_sat ? -a.msg_sat : (int)rr);
+            }
+            A[j * Z + r] = (int8_t)q;
+        }
+        for (int b = 0; b < nnz; b++) Rc[b * Z + r] = 0;
+    };
+
+    int64_t cw = mine ? fresh[c] : -1;
+    int t = 0;
+    if (cw >= 0) refill(cw);
+    if (!group_any(cw >= 0)) return;
 
     for (;;) {
-        if (r == 0) {
-            const unsigned long long k = atomicAdd(a.next, 1ull);
-            fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
-        }
-        lslot_sync(c, TPS);  // also: every thread is done with the previous codeword
-        const int64_t cw = fresh[c];
-        if (cw < 0) break;
-        if (r == 0) flag[2 * c] = flag[2 * c + 1] = 0;
-        if (row) {
-            for (int j = 0; j < nb; j++) {
-                const int64_t i = cw * N + j * Z + r;
-                int q;
-                if (a.llr_type == LDPC_LLR_I8) {
-                    const int raw = static_cast<const int8_t *>(a.llr)[i];
-                    if (raw < -a.msg_sat || raw > a.msg_sat) atomicOr(cd->status, IN_I8_RANGE);
-                    q = sat_i(raw, a.msg_sat);
-                } else {
-                    const float in = __ldg(static_cast<const float *>(a.llr) + i);
-                    if (!isfinite(in)) atomicOr(cd->status, IN_NONFINITE);
-                    const float rr = rintf(__fmul_rn(a.scale, in));
-                    q = rr > (float)a.msg_sat ? a.msg_sat : (rr < -(float)a.msg_sat ? -a.msg_sat : (int)rr);
+        const bool busy = cw >= 0;
+        for (int l = 0; l < mb; l++) {
+            if (busy) {
+                const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
+                int8_t *Rr = Rc + b0 * Z + r;
+                int qx[DMAX];  // (wrapped position << 8) | (Q & 0xff): one register per edge
+                int min1 = 0x7fffffff, min2 = 0x7fffffff, arg = -1;
+                unsigned S = 0;
+#pragma unroll
+                for (int k = 0; k < DMAX; k++) {
+                    if (k < dc) {
+                        const int ent = t_ent[b0 + k];
+                        int x = r + (ent >> 16);
+                        x -= (x >= Z) ? Z : 0;
+                        const int qq = sat_i((int)A[(ent & 0xffff) + x] - (int)Rr[k * Z], a.msg_sat);
+                        const int mag = qq < 0 ? -qq : qq;
+                        if (mag < min1) {
+                            min2 = min1;
+                            min1 = mag;
+                            arg = k;
+                        } else if (mag < min2) {
+                            min2 = mag;
+                        }
+                        S ^= qq < 0 ? 1u : 0u;
+                        qx[k] = (x << 8) | (qq & 0xff);
+                    }
                 }
-                A[j * Z + r] = (int8_t)q;
+                const int m1 = (a.alpha_num * min1) >> a.alpha_shift;
+                const int m2 = (a.alpha_num * min2) >> a.alpha_shift;
+#pragma unroll
+                for (int k = 0; k < DMAX; k++) {
+                    if (k < dc) {
+                        const int qq = (int)(int8_t)(qx[k] & 0xff);
+                        const int x = qx[k] >> 8;
+                        const int magp = (k == arg) ? m2 : m1;
+                        const int rn = (S ^ (qq < 0 ? 1u : 0u)) ? -magp : magp;
+                        Rr[k * Z] = (int8_t)rn;
+                        A[(t_ent[b0 + k] & 0xffff) + x] = (int8_t)sat_i(qq + rn, a.app_sat);
+                    }
+                }
             }
-            for (int b = 0; b < nnz; b++) Rc[b * Z + r] = 0;
+            lgroup_sync(g, TPG);
         }
-        lslot_sync(c, TPS);
-        int t = 0;
-        for (;;) {
+        if (busy) t++;
+        // syndrome of the hard decisions: row r of every layer
+        if (busy && a.early_exit) {
+            unsigned par_any = 0;
             for (int l = 0; l < mb; l++) {
-                if (row) {
-                    const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
-                    int8_t *Rr = Rc + b0 * Z + r;
-                    int qx[DMAX];  // (wrapped position << 8) | (Q & 0xff): one register per edge
-                    int min1 = 0x7fffffff, min2 = 0x7fffffff, arg = -1;
-                    unsigned S = 0;
-#pragma unroll
-                    for (int k = 0; k < DMAX; k++) {
-                        if (k < dc) {
-                            const int ent = t_ent[b0 + k];
-                            int x = r + (ent >> 16);
-                            x -= (x >= Z) ? Z : 0;
-                            const int qq = sat_i((int)A[(ent & 0xffff) + x] - (int)Rr[k * Z], a.msg_sat);
-                            const int mag = qq < 0 ? -qq : qq;
-                            if (mag < min1) {
-                                min2 = min1;
-                                min1 = mag;
-                                arg = k;
-                            } else if (mag < min2) {
-                                min2 = mag;
-                            }
-                            S ^= qq < 0 ? 1u : 0u;
-                            qx[k] = (x << 8) | (qq & 0xff);
-                        }
-                    }
-                    const int m1 = (a.alpha_num * min1) >> a.alpha_shift;
-                    const int m2 = (a.alpha_num * min2) >> a.alpha_shift;
-#pragma unroll
-                    for (int k = 0; k < DMAX; k++) {
-                        if (k < dc) {
-                            const int qq = (int)(int8_t)(qx[k] & 0xff);
-                            const int x = qx[k] >> 8;
-                            const int magp = (k == arg) ? m2 : m1;
-                            const int rn = (S ^ (qq < 0 ? 1u : 0u)) ? -magp : magp;
-                            Rr[k * Z] = (int8_t)rn;
-                            A[(t_ent[b0 + k] & 0xffff) + x] = (int8_t)sat_i(qq + rn, a.app_sat);
-                        }
-                    }
+                unsigned par = 0;
+                for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++) {
+                    const int ent = t_ent[b];
+                    int x = r + (ent >> 16);
+                    x -= (x >= Z) ? Z : 0;
+                    par ^= A[(ent & 0xffff) + x] < 0 ? 1u : 0u;
                 }
-                lslot_sync(c, TPS);
+                par_any |= par;
             }
-            t++;
-            bool conv = false;
-            if (a.early_exit) {
-                // syndrome of the hard decisions: row r of every layer; the iteration's flag
-                // alternates so that clearing the next one races with nothing
-                if (row) {
-                    unsigned par_any = 0;
-                    for (int l = 0; l < mb; l++) {
-                        unsigned par = 0;
-                        for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++) {
-                            const int ent = t_ent[b];
-                            int x = r + (ent >> 16);
-                            x -= (x >= Z) ? Z : 0;
-                            par ^= A[(ent & 0xffff) + x] < 0 ? 1u : 0u;
-                        }
-                        par_any |= par;
-                    }
-                    if (par_any) flag[2 * c + (t & 1)] = 1;
+            if (par_any) bad[c] = 1;
+        }
+        lgroup_sync(g, TPG);
+        bool done = false;
+        if (busy) {
+            done = (a.early_exit && bad[c] == 0) || t >= a.max_iter;
+            if (done) {
+                uint8_t *Bo = a.bits + cw * N;
+                float *Ao = a.app_out ? a.app_out + cw * N : nullptr;
+                for (int j = 0; j < nb; j++) {
+                    const int v = A[j * Z + r];
+                    Bo[j * Z + r] = v < 0 ? 1 : 0;
+                    if (Ao) Ao[j * Z + r] = (float)v;
                 }
-                lslot_sync(c, TPS);
-                conv = flag[2 * c + (t & 1)] == 0;
-                if (r == 0) flag[2 * c + ((t + 1) & 1)] = 0;
+                if (r == 0) {
+                    a.iters[cw] = t;
+                    const unsigned long long k = atomicAdd(a.next, 1ull);
+                    fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+                }
             }
-            if (conv || t >= a.max_iter) break;
         }
-        if (row) {
-            uint8_t *Bo = a.bits + cw * N;
-            float *Ao = a.app_out ? a.app_out + cw * N : nullptr;
-            for (int j = 0; j < nb; j++) {
-                const int v = A[j * Z + r];
-                Bo[j * Z + r] = v < 0 ? 1 : 0;
-                if (Ao) Ao[j * Z + r] = (float)v;
+        lgroup_sync(g, TPG);
+        if (busy) {
+            if (r == 0) bad[c] = 0;
+            if (done) {
+                cw = fresh[c];
+                t = 0;
+                if (cw >= 0) refill(cw);
             }
-            if (r == 0) a.iters[cw] = t;
         }
+        if (!group_any(cw >= 0)) break;
     }
 }
 
@@ -370,23 +398,35 @@ static cudaError_t launch_layered(const CodeDev &h, const CodeDev *d, const Laye
     return cudaGetLastError();
 }
 
-static int lslots_tps(const CodeDev &h) { return ((h.Z + 31) / 32) * 32; }
-
 static size_t lslots_smem(const CodeDev &h, int C)
 {
     return slots_smem_head(h.nnz + h.mb + 1) + (size_t)C * (((h.N + 15) & ~15) + ((h.E + 15) & ~15));
 }
 
-int layered_slots_per_cta(const CodeDev &h)
+// Slots per CTA and their grouping: the most slots that fit 1024 threads, 15 named barriers
+// and the shared-memory budget, with the fewest slots per group among the arrangements that
+// reach that count (fewer idle lanes first, then more independence).
+struct LslotShape {
+    int C, K, TPG;
+};
+static LslotShape lslots_shape(const CodeDev &h)
 {
-    if (h.dc_max > 32 || h.N >= 65536) return 0;
-    const int tps = lslots_tps(h);
-    int C = 1024 / tps;
-    if (C > SLOTS_MAX) C = SLOTS_MAX;
-    if (tps > 32 && C > 15) C = 15;  // named barriers 1..15
-    while (C > 0 && lslots_smem(h, C) > 200 * 1024) C--;
-    return C;
+    LslotShape best = {0, 1, 32};
+    if (h.dc_max > 32 || h.N >= 65536) return best;
+    int cmax = SLOTS_MAX;
+    while (cmax > 0 && lslots_smem(h, cmax) > 200 * 1024) cmax--;
+    for (int K = 1; K <= cmax; K++) {
+        const int tpg = ((K * h.Z + 31) / 32) * 32;
+        int G = 1024 / tpg;
+        if (tpg > 32 && G > 15) G = 15;
+        int C = G * K;
+        if (C > cmax) C = cmax;
+        if (C > best.C) best = {C, K, tpg};
+    }
+    return best;
 }
+
+int layered_slots_per_cta(const CodeDev &h) { return lslots_shape(h).C; }
 
 template <int DMAX>
 static cudaError_t launch_lslots(const CodeDev &h, const CodeDev *d, const LayeredSlotArgs &a, cudaStream_t s)
@@ -401,7 +441,8 @@ static cudaError_t launch_lslots(const CodeDev &h, const CodeDev *d, const Layer
     const int64_t need = (a.n_cw + a.C - 1) / a.C;
     if (need < ctas) ctas = need;
     LaunchScope ls(F_LAYERED, s);
-    k_layered_slots<DMAX><<<(unsigned)ctas, a.C * a.TPS, sm, s>>>(d, a);
+    const int groups = (a.C + a.K - 1) / a.K;
+    k_layered_slots<DMAX><<<(unsigned)ctas, groups * a.TPG, sm, s>>>(d, a);
     return cudaGetLastError();
 }
 
@@ -414,9 +455,11 @@ cudaError_t layered_slots_decode(const CodeDev &h, const CodeDev *d, const ldpc_
     a.llr_type = llr_type;
     a.scale = p.llr_scale;
     a.n_cw = n_cw;
-    a.C = layered_slots_per_cta(h);
+    const LslotShape sh = lslots_shape(h);
+    a.C = sh.C;
     if (a.C < 1) return cudaErrorInvalidValue;
-    a.TPS = lslots_tps(h);
+    a.K = sh.K;
+    a.TPG = sh.TPG;
     a.strideA = (h.N + 15) & ~15;
     a.strideR = (h.E + 15) & ~15;
     a.max_iter = p.max_iter;
