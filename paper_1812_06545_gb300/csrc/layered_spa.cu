@@ -3,12 +3,14 @@
 //
 // A persistent grid of one CTA per SM.  Each CTA holds C codeword slots; a slot keeps its
 // posterior APP [N] (fp32) and its check-to-variable messages R [E] (fp32 or fp16) in
-// shared memory for the whole decode of one codeword.  A slot owns whole warps
-// (ceil(Z/32) of them) and thread r of the slot owns check row r of every block row
-// (layer).  The Z checks of a QC layer touch disjoint variables (each block is one
-// circulant), so the row threads update a layer at once and the slot's own barrier (a
-// named barrier, or the warp itself when Z <= 32) separates consecutive layers: slots run
-// independently, each at its own codeword and iteration, with no CTA-wide lock-step.
+// shared memory for the whole decode of one codeword.  The slots form barrier groups of K:
+// a group's threads cover its K*Z check rows packed into whole warps, and thread u of a
+// group owns check row u mod Z of slot u / Z, for every block row (layer).  The Z checks of
+// a QC layer touch disjoint variables (each block is one circulant), so the row threads
+// update a layer at once and the group's own barrier (a named barrier, or the warp itself
+// when the group is one warp) separates consecutive layers: the slots of a group run in
+// lock-step, the groups independently, with no CTA-wide barrier.  K trades the idle lanes
+// of a warp-aligned slot (Z not a multiple of 32) against waiting for a group's slowest slot.
 // Messages are stored in check-row order, edge (b, r) at b*Z + r: the layered schedule has
 // no variable-node pass, so the row threads of a warp read and write them contiguously.
 // Per check (the arithmetic of the flooding slot decoder, only the schedule differs):
@@ -17,9 +19,9 @@
 //           (stored as fp16 when the messages are half precision)
 //   APP_n = Q_k + R'_k   with R'_k the stored value, so that the next Q = APP - R removes
 //                        exactly what was added
-// After every full iteration the slot's hard decisions are checked against all of its
+// After every full iteration each slot's hard decisions are checked against all of its
 // checks; a slot that converged (early exit) or reached max_iter writes its outputs and
-// takes the next codeword from the global work counter.
+// takes the next codeword from the global work counter at its group's next iteration.
 //
 // APP is never -0: the refill adds +0 to the channel value and Q + R' is -0 only when both
 // are -0, which cannot happen while APP is not -0 (then Q = APP - R is not -0).  The sign
@@ -32,7 +34,7 @@ struct LayeredSpaArgs {
     const float *llr;
     int64_t n_cw;
     int C, strideA, strideR;  // slots per CTA; per-slot APP and R strides (elements)
-    int TPS;                  // threads per slot: whole warps covering Z rows
+    int K, TPG;               // slots per barrier group; threads per group (whole warps)
     int max_iter, early_exit;
     float X;
     uint8_t *bits;
@@ -184,14 +186,14 @@ constexpr int lspa_threads_max()
     return sizeof(MsgT) == 4 ? (DMAX <= 16 ? 672 : 512) : (DMAX <= 8 ? 1024 : (DMAX <= 16 ? 768 : 512));
 }
 
-// The barrier of one slot: its warps only (named barrier slot + 1; barrier 0 is the CTA's),
-// or nothing beyond the warp itself when the slot is one warp.
-__device__ __forceinline__ void slot_sync(int slot, int tps)
+// The barrier of one slot group: its warps only (named barrier group + 1; barrier 0 is the
+// CTA's), or nothing beyond the warp itself when the group is one warp.
+__device__ __forceinline__ void group_sync(int grp, int tpg)
 {
-    if (tps == 32)
+    if (tpg == 32)
         __syncwarp();
     else
-        asm volatile("bar.sync %0, %1;" ::"r"(slot + 1), "r"(tps) : "memory");
+        asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(tpg) : "memory");
 }
 
 template <int DMAX, typename MsgT>
@@ -200,10 +202,11 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = cd->N, Z = cd->Z, mb = cd->mb, nb = cd->nb, nnz = cd->nnz;
-    const int C = a.C, TPS = a.TPS;
-    int32_t *flag = reinterpret_cast<int32_t *>(smem);               // [SLOTS_MAX][2] unsatisfied check seen
-    int64_t *fresh = reinterpret_cast<int64_t *>(flag + 2 * SLOTS_MAX);  // [SLOTS_MAX] the slot's codeword
-    int32_t *t_ent = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);  // (s << 16) | j*Z per block
+    const int C = a.C, K = a.K, TPG = a.TPG;
+    int32_t *bad = reinterpret_cast<int32_t *>(smem);                 // [SLOTS_MAX] unsatisfied check seen
+    int32_t *gany = bad + SLOTS_MAX;                                   // [SLOTS_MAX / 2][2] group vote
+    int64_t *fresh = reinterpret_cast<int64_t *>(gany + SLOTS_MAX);    // [SLOTS_MAX] the slot's codeword
+    int32_t *t_ent = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);   // (s << 16) | j*Z per block
     int32_t *t_rowptr = t_ent + nnz;
     float *APPs = reinterpret_cast<float *>(smem + slots_smem_head(nnz + mb + 1));
     MsgT *Rs = reinterpret_cast<MsgT *>(APPs + (size_t)C * a.strideA);
@@ -215,81 +218,103 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
         t_ent[i] = ((e & 0xffff) << 16) | ((e >> 16) * Z);
     }
     for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
+    const int g = tid / TPG, u = tid - (tid / TPG) * TPG;
+    const int c = g * K + u / Z, r = u - (u / Z) * Z;
+    const bool mine = u < K * Z && c < C;  // a row of a slot (else an idle lane of the group)
+    if (tid == 0)
+        for (int i = 0; i < SLOTS_MAX; i++) gany[i] = 0;
+    if (mine && r == 0) {
+        const unsigned long long k = atomicAdd(a.next, 1ull);
+        fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+        bad[c] = 0;
+    }
     __syncthreads();
+    if (g * K >= C) return;  // whole warps beyond the last group
+    float *A = APPs + (size_t)(mine ? c : 0) * a.strideA;
+    MsgT *Rc = Rs + (size_t)(mine ? c : 0) * a.strideR;
+    int ph = 0;
+    // OR of a predicate over the group (every thread of the group calls it at the same
+    // point; the vote alternates between two words so that clearing the next one races with
+    // nothing)
+    auto group_any = [&](bool pred) {
+        if (pred) gany[2 * g + ph] = 1;
+        group_sync(g, TPG);
+        const bool any = gany[2 * g + ph] != 0;
+        if (u == 0) gany[2 * g + (ph ^ 1)] = 0;
+        ph ^= 1;
+        return any;
+    };
 
-    const int c = tid / TPS, r = tid - (tid / TPS) * TPS;
-    if (c >= C) return;  // whole warps beyond the last slot (none when blockDim = C * TPS)
-    const bool row = r < Z;
-    float *A = APPs + (size_t)c * a.strideA;
-    MsgT *Rc = Rs + (size_t)c * a.strideR;
+    // a slot given codeword k loads APP = L (+0: no -0 in APP) and clears its messages
+    auto refill = [&](int64_t k) {
+        const float *L = a.llr + k * N;
+        for (int j = 0; j < nb; j++) {
+            const float v = __ldg(L + j * Z + r);
+            if (!isfinite(v)) atomicOr(cd->status, IN_NONFINITE);
+            A[j * Z + r] = v + 0.0f;
+        }
+        for (int b = 0; b < nnz; b++) Rc[b * Z + r] = MsgT(0.0f);
+    };
+
+    int64_t cw = mine ? fresh[c] : -1;
+    int t = 0;
+    if (cw >= 0) refill(cw);
+    if (!group_any(cw >= 0)) return;
 
     for (;;) {
-        if (r == 0) {
-            const unsigned long long k = atomicAdd(a.next, 1ull);
-            fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
-        }
-        slot_sync(c, TPS);  // also: every thread is done with the previous codeword
-        const int64_t cw = fresh[c];
-        if (cw < 0) break;
-        if (r == 0) flag[2 * c] = flag[2 * c + 1] = 0;
-        // load the codeword: APP = L (+0: no -0 in APP), messages cleared
-        if (row) {
-            const float *L = a.llr + cw * N;
-            for (int j = 0; j < nb; j++) {
-                const float v = __ldg(L + j * Z + r);
-                if (!isfinite(v)) atomicOr(cd->status, IN_NONFINITE);
-                A[j * Z + r] = v + 0.0f;
+        const bool busy = cw >= 0;
+        for (int l = 0; l < mb; l++) {
+            if (busy) {
+                const int b0 = t_rowptr[l];
+                layer_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ent + b0, b0 * Z, A, Rc, r, Z, X, Xb);
             }
-            for (int b = 0; b < nnz; b++) Rc[b * Z + r] = MsgT(0.0f);
+            group_sync(g, TPG);
         }
-        slot_sync(c, TPS);
-        int t = 0;
-        for (;;) {
+        if (busy) t++;
+        // syndrome of the hard decisions (APP sign bits): row r of every layer
+        if (busy && a.early_exit) {
+            uint32_t par_any = 0;
             for (int l = 0; l < mb; l++) {
-                if (row) {
-                    const int b0 = t_rowptr[l];
-                    layer_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ent + b0, b0 * Z, A, Rc, r, Z, X,
-                                                        Xb);
+                uint32_t par = 0;
+                for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++) {
+                    const int e = t_ent[b];
+                    int x = r + (e >> 16);
+                    x -= (x >= Z) ? Z : 0;
+                    par ^= __float_as_uint(A[(e & 0xffff) + x]);
                 }
-                slot_sync(c, TPS);
+                par_any |= par;
             }
-            t++;
-            // syndrome of the hard decisions (APP sign bits): row r of every layer; the
-            // iteration's flag alternates so that clearing the next one races with nothing
-            bool conv = false;
-            if (a.early_exit) {
-                if (row) {
-                    uint32_t par_any = 0;
-                    for (int l = 0; l < mb; l++) {
-                        uint32_t par = 0;
-                        for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++) {
-                            const int e = t_ent[b];
-                            int x = r + (e >> 16);
-                            x -= (x >= Z) ? Z : 0;
-                            par ^= __float_as_uint(A[(e & 0xffff) + x]);
-                        }
-                        par_any |= par;
-                    }
-                    if (par_any & 0x80000000u) flag[2 * c + (t & 1)] = 1;
+            if (par_any & 0x80000000u) bad[c] = 1;
+        }
+        group_sync(g, TPG);
+        bool done = false;
+        if (busy) {
+            done = (a.early_exit && bad[c] == 0) || t >= a.max_iter;
+            if (done) {
+                uint8_t *Bo = a.bits + cw * N;
+                float *Ao = a.app_out ? a.app_out + cw * N : nullptr;
+                for (int j = 0; j < nb; j++) {
+                    const float v = A[j * Z + r];
+                    Bo[j * Z + r] = v < 0.0f ? 1 : 0;
+                    if (Ao) Ao[j * Z + r] = v;
                 }
-                slot_sync(c, TPS);
-                conv = flag[2 * c + (t & 1)] == 0;
-                if (r == 0) flag[2 * c + ((t + 1) & 1)] = 0;
+                if (r == 0) {
+                    a.iters[cw] = t;
+                    const unsigned long long k = atomicAdd(a.next, 1ull);
+                    fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+                }
             }
-            if (conv || t >= a.max_iter) break;
         }
-        if (row) {
-            uint8_t *Bo = a.bits + cw * N;
-            float *Ao = a.app_out ? a.app_out + cw * N : nullptr;
-            for (int j = 0; j < nb; j++) {
-                const float v = A[j * Z + r];
-                Bo[j * Z + r] = v < 0.0f ? 1 : 0;
-                if (Ao) Ao[j * Z + r] = v;
+        group_sync(g, TPG);
+        if (busy) {
+            if (r == 0) bad[c] = 0;
+            if (done) {
+                cw = fresh[c];
+                t = 0;
+                if (cw >= 0) refill(cw);
             }
-            if (r == 0) a.iters[cw] = t;
         }
-        // the next codeword is announced before the barrier at the top of the loop and the
-        // flags are cleared after it, when every thread has finished with this codeword
+        if (!group_any(cw >= 0)) break;
     }
 }
 
@@ -313,22 +338,35 @@ static size_t lspa_smem(const CodeDev &h, int msg, int C)
     return slots_smem_head(h.nnz + h.mb + 1) + (size_t)C * lspa_slot_bytes(h, msg);
 }
 
-static int lspa_tps(const CodeDev &h) { return ((h.Z + 31) / 32) * 32; }
-
-int layered_spa_slots_per_cta(const CodeDev &h, int msg)
+// Slots per CTA and their grouping: the most slots that fit the instance's threads, 15 named
+// barriers and shared memory, with the fewest slots per group among the arrangements that
+// reach that count.
+struct LspaShape {
+    int C, K, TPG;
+};
+static LspaShape lspa_shape(const CodeDev &h, int msg)
 {
-    if (h.dc_max > 32 || h.N >= 65536) return 0;
-    const int tps = lspa_tps(h);
-    int C = lspa_threads_for(h.dc_max, msg) / tps;
-    if (C > SLOTS_MAX) C = SLOTS_MAX;
-    if (tps > 32 && C > 15) C = 15;  // named barriers 1..15
+    LspaShape best = {0, 1, 32};
+    if (h.dc_max > 32 || h.N >= 65536) return best;
     int dev = 0, lim = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const size_t limit = lim > 0 ? (size_t)lim : 227 * 1024;
-    while (C > 0 && lspa_smem(h, msg, C) > limit) C--;
-    return C;
+    int cmax = SLOTS_MAX;
+    while (cmax > 0 && lspa_smem(h, msg, cmax) > limit) cmax--;
+    const int tmax = lspa_threads_for(h.dc_max, msg);
+    for (int K = 1; K <= cmax; K++) {
+        const int tpg = ((K * h.Z + 31) / 32) * 32;
+        int G = tmax / tpg;
+        if (tpg > 32 && G > 15) G = 15;
+        int C = G * K;
+        if (C > cmax) C = cmax;
+        if (C > best.C) best = {C, K, tpg};
+    }
+    return best;
 }
+
+int layered_spa_slots_per_cta(const CodeDev &h, int msg) { return lspa_shape(h, msg).C; }
 
 template <int DMAX, typename MsgT>
 static cudaError_t launch_lspa(const CodeDev &h, const CodeDev *d, const LayeredSpaArgs &a, int msg, cudaStream_t s)
@@ -343,7 +381,8 @@ static cudaError_t launch_lspa(const CodeDev &h, const CodeDev *d, const Layered
     const int64_t need = (a.n_cw + a.C - 1) / a.C;
     if (need < ctas) ctas = need;
     LaunchScope ls(F_LAYERED_SPA, s);
-    k_layered_spa<DMAX, MsgT><<<(unsigned)ctas, a.C * a.TPS, sm, s>>>(d, a);
+    const int groups = (a.C + a.K - 1) / a.K;
+    k_layered_spa<DMAX, MsgT><<<(unsigned)ctas, groups * a.TPG, sm, s>>>(d, a);
     return cudaGetLastError();
 }
 
@@ -363,9 +402,11 @@ cudaError_t layered_spa_decode(const CodeDev &h, const CodeDev *d, const ldpc_de
     LayeredSpaArgs a;
     a.llr = llr;
     a.n_cw = n_cw;
-    a.C = layered_spa_slots_per_cta(h, p.msg);
+    const LspaShape sh = lspa_shape(h, p.msg);
+    a.C = sh.C;
     if (a.C < 1) return cudaErrorInvalidValue;
-    a.TPS = lspa_tps(h);
+    a.K = sh.K;
+    a.TPG = sh.TPG;
     a.strideA = (h.N + 3) & ~3;
     a.strideR = (h.E + 7) & ~7;
     a.max_iter = p.max_iter;
