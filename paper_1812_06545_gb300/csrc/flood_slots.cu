@@ -36,6 +36,10 @@
 
 namespace ldpc {
 
+#ifndef LDPC_REFILL_CHUNK
+#define LDPC_REFILL_CHUNK 8  // channel values a thread loads at once when a slot takes a codeword
+#endif
+
 // Per-slot strides of APP and R (elements): at least the length, and congruent to Z modulo
 // the 32 shared-memory banks, so that a warp whose rows run from the end of one slot group
 // into the start of the next sees the two groups' rows as one contiguous bank sequence.
@@ -131,13 +135,13 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
         // load a new codeword into slot v, this thread's columns: APP = L (+0 for -0), R = 0
         auto refill = [&](int v) {
             const float *Lr = static_cast<const float *>(a.d.reqs[rq[v]].llr) + cw[v] * N;
-            for (int j0 = 0; j0 < nb; j0 += 8) {
-                float x[8];
+            for (int j0 = 0; j0 < nb; j0 += LDPC_REFILL_CHUNK) {
+                float x[LDPC_REFILL_CHUNK];
 #pragma unroll
-                for (int u = 0; u < 8; u++)
+                for (int u = 0; u < LDPC_REFILL_CHUNK; u++)
                     if (j0 + u < nb) x[u] = __ldg(Lr + (j0 + u) * Z + r);
 #pragma unroll
-                for (int u = 0; u < 8; u++)
+                for (int u = 0; u < LDPC_REFILL_CHUNK; u++)
                     if (j0 + u < nb) {
                         if (!isfinite(x[u])) atomicOr(cd->status, IN_NONFINITE);
                         A[((j0 + u) * Z + r) * V + v] = x[u] + 0.0f;
