@@ -50,13 +50,18 @@ typedef enum { LDPC_LLR_F32 = 0, LDPC_LLR_I8 = 1 } ldpc_llr_type;
 typedef enum {
     LDPC_IMPL_AUTO = 0,     /* the fastest kernels for the requested form: for flooding, the */
                             /* on-chip slot decoder when one codeword's posterior and        */
-                            /* messages fit in shared memory, else the streaming kernels     */
+                            /* messages fit in shared memory, else the cluster decoder when  */
+                            /* they fit two SMs, else the streaming kernels                  */
     LDPC_IMPL_PLAIN = 1,    /* the plain FP32 flooding comparator (one codeword per thread,  */
                             /* library expm1f/log1pf phi, state streamed through HBM)        */
-    LDPC_IMPL_STREAMING = 2 /* flooding with all state streamed through HBM in the          */
-                            /* codeword-interleaved layout (check-node and variable-node    */
-                            /* kernels per iteration); layered min-sum with a fixed group of */
-                            /* codewords per CTA instead of persistent refilled slots        */
+    LDPC_IMPL_STREAMING = 2, /* flooding with all state streamed through HBM in the         */
+                             /* codeword-interleaved layout (check-node and variable-node   */
+                             /* kernels per iteration); layered min-sum with a fixed group  */
+                             /* of codewords per CTA instead of persistent refilled slots   */
+    LDPC_IMPL_CLUSTER = 3    /* flooding SPA on the cluster decoder: one codeword per two-SM */
+                             /* thread-block cluster, its rows and columns split between the */
+                             /* two CTAs' shared memories (AUTO uses it when a codeword does */
+                             /* not fit one CTA but fits a cluster)                          */
 } ldpc_impl;
 
 /* Opaque code object (library-owned, immutable after creation, usable from any thread). */

@@ -1,0 +1,326 @@
+// Flooding sum-product decoding of codes too large for one SM: the cluster slot decoder.
+//
+// A thread-block cluster of CL CTAs (CL SMs) holds one codeword for the whole decode, split
+// between its CTAs: CTA q owns a contiguous range of block rows (their checks and the
+// messages R of their edges) and a contiguous range of block columns (their posteriors
+// APP).  The two ranges are balanced by block count.  A check of CTA q reads the posteriors
+// of its variables wherever they live (distributed shared memory of the cluster); a variable
+// of CTA q reads the messages of its edges wherever they live.  One round (Sec. II two-phase
+// message passing, Algorithm 1 loop order), each phase closed by a cluster barrier:
+//   check-node phase   every owned check: Q = APP - R, R' from the phi rule (the arithmetic
+//                      of the slot decoders), written in place; the parity of the APP sign
+//                      bits over the check flags an unsatisfied check of the previous
+//                      iteration's decisions
+//   decision           no CTA of the cluster flagged a check and >= 1 iteration done: the
+//                      codeword has converged (its APP from that iteration is final)
+//   variable-node phase otherwise every owned variable: APP = L + sum of the new R
+// A finished codeword is written out and the cluster's leader takes the next codeword from
+// the global work counter.  Messages sit in check-row order, edge (b, r) of the owned block b
+// at (b - first owned block) * Z + r; posteriors at (j - first owned column) * Z + c.
+#include <string.h>
+
+#include <cooperative_groups.h>
+
+#include "slot_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ldpc {
+
+constexpr int CLUSTER_CTAS = 2;
+
+struct ClusterArgs {
+    const float *llr;
+    uint8_t *bits;
+    int32_t *iters;
+    float *app_out;
+    int64_t n_cw;
+    unsigned long long *next;
+    int row_split[CLUSTER_CTAS + 1];  // block rows [row_split[q], row_split[q+1]) belong to CTA q
+    int col_split[CLUSTER_CTAS + 1];  // block columns likewise
+    int max_iter, early_exit;
+    float X;
+};
+
+__host__ __device__ inline int cl_owner(const int *split, int x)
+{
+    int q = 0;
+    while (q < CLUSTER_CTAS - 1 && x >= split[q + 1]) q++;
+    return q;
+}
+
+// threads per CTA: higher check degrees keep more values live per thread
+template <int DMAX>
+constexpr int cl_threads() { return DMAX <= 8 ? 1024 : (DMAX <= 16 ? 768 : 512); }
+
+template <int DMAX, typename MsgT>
+__global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_threads<DMAX>(), 1)
+    k_flood_cluster(const CodeDev *__restrict__ cd, const __grid_constant__ ClusterArgs a)
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int q = (int)cluster.block_rank();
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int Z = cd->Z, mb = cd->mb, nb = cd->nb, nnz = cd->nnz;
+    const float X = a.X, Xb = a.X * kSLog2e;
+
+    // bookkeeping: [0] bad flags (2, alternating by round), [2] codeword (int64 at 8)
+    int32_t *flags = reinterpret_cast<int32_t *>(smem);
+    int64_t *cwp = reinterpret_cast<int64_t *>(smem + 8);
+    int32_t *t_rowptr = reinterpret_cast<int32_t *>(smem + 16);  // [mb + 1]
+    int32_t *t_ent = t_rowptr + MB_MAX + 1;                       // [nnz] (shift << 20) | owner APP base
+    int32_t *t_colptr = t_ent + NNZ_MAX;                          // [nb + 1]
+    int32_t *t_cent = t_colptr + NB_MAX + 1;                      // [nnz] (shift << 20) | owner R base
+    int32_t *t_cown = t_cent + NNZ_MAX;                           // [nnz] owner of the entry's row
+    const int col0 = a.col_split[q], col1 = a.col_split[q + 1];
+    const int row0 = a.row_split[q], row1 = a.row_split[q + 1];
+    // block b's owner of posteriors and its base there; column entry's owner of messages
+    for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
+    for (int i = tid; i <= nb; i += nth) t_colptr[i] = cd->colptr[i];
+    __syncthreads();
+    const int blk0 = t_rowptr[row0], blk1 = t_rowptr[row1];
+    for (int b = tid; b < nnz; b += nth) {
+        const int e = cd->ent[b];
+        const int j = e >> 16, s = e & 0xffff;
+        const int qo = cl_owner(a.col_split, j);
+        t_ent[b] = (s << 20) | (qo << 19) | ((j - a.col_split[qo]) * Z);
+    }
+    for (int i = tid; i < nnz; i += nth) {
+        const int ce = cd->colent[i];
+        const int b = ce >> 16, s = ce & 0xffff;
+        int l = 0;
+        while (l < mb - 1 && b >= cd->rowptr[l + 1]) l++;
+        const int qo = cl_owner(a.row_split, l);
+        t_cent[i] = (s << 20) | ((b - cd->rowptr[a.row_split[qo]]) * Z);
+        t_cown[i] = qo;
+    }
+    const size_t off_app = (((size_t)(16 + 4 * (2 * NNZ_MAX + MB_MAX + NB_MAX + 2 + NNZ_MAX))) + 15) & ~(size_t)15;
+    float *app = reinterpret_cast<float *>(smem + off_app);
+    // R starts at the same offset in every CTA (after the largest posterior share), so that
+    // mapping an address into another CTA of the cluster finds that CTA's messages
+    int napp_max = 0;
+#pragma unroll
+    for (int k = 0; k < CLUSTER_CTAS; k++) {
+        const int na = (a.col_split[k + 1] - a.col_split[k]) * Z;
+        napp_max = na > napp_max ? na : napp_max;
+    }
+    MsgT *R = reinterpret_cast<MsgT *>(smem + off_app + (((size_t)napp_max * 4 + 15) & ~(size_t)15));
+    // the cluster's posterior and message arrays, by owning CTA (generic pointers; the own
+    // CTA's are plain shared memory)
+    static_assert(CLUSTER_CTAS == 2, "the owner selects below assume two CTAs");
+    const float *app_0 = cluster.map_shared_rank(app, 0), *app_1 = cluster.map_shared_rank(app, 1);
+    const MsgT *r_0 = cluster.map_shared_rank(R, 0), *r_1 = cluster.map_shared_rank(R, 1);
+    const int n_check = (row1 - row0) * Z, n_var = (col1 - col0) * Z;
+    int64_t *cw0 = cluster.map_shared_rank(cwp, 0);
+    cluster.sync();  // tables built in every CTA before any remote access
+
+    for (;;) {
+        // the leader (CTA 0, thread 0) takes the next codeword; every CTA reads it
+        if (q == 0 && tid == 0) {
+            const unsigned long long k = atomicAdd(a.next, 1ull);
+            cwp[0] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+        }
+        cluster.sync();  // also: no CTA still reads another's flags of the previous codeword
+        const int64_t cw = *cw0;
+        if (cw < 0) break;
+        if (tid == 0) flags[0] = flags[1] = 0;
+        // load: APP = L (+0: no -0) for owned variables, R = 0 for owned edges
+        const float *L = a.llr + cw * cd->N;
+        for (int i = tid; i < n_var; i += nth) {
+            const float v = __ldg(L + col0 * Z + i);
+            if (!isfinite(v)) atomicOr(cd->status, IN_NONFINITE);
+            app[i] = v + 0.0f;
+        }
+        for (int i = tid; i < (blk1 - blk0) * Z; i += nth) R[i] = MsgT(0.0f);
+        cluster.sync();
+        int t = 0;
+        bool done = false;
+        while (!done) {
+            const int tr = t;  // this round's flag is flags[tr & 1]
+            // ---------------- check-node phase over the owned checks
+            bool pbad = false;
+            for (int w = tid; w < n_check; w += nth) {
+                const int lr = w / Z, r = w - lr * Z;
+                const int l = row0 + lr;
+                const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
+                MsgT *Rr = R + (b0 - blk0) * Z + r;
+                float av[DMAX];
+                uint32_t sg = 0, par = 0;
+                float S = 0.0f, amax = 0.0f;
+#pragma unroll
+                for (int k = 0; k < DMAX; k++) {
+                    if (k < dc) {
+                        const int e = t_ent[b0 + k];
+                        int x = r + (e >> 20);
+                        x -= (x >= Z) ? Z : 0;
+                        const float ap = ((e >> 19) & 1 ? app_1 : app_0)[(e & 0x7ffff) + x];
+                        const float rv = (float)Rr[k * Z];
+                        const float qv = ap - rv;
+                        par ^= __float_as_uint(ap);
+                        const float m = fminf(s_psi_in(fminf(fabsf(qv), X)), Xb);
+                        const uint32_t qs = __float_as_uint(qv) & kSign;
+                        sg ^= qs;
+                        S += m;
+                        amax = fmaxf(amax, m);
+                        av[k] = __uint_as_float(__float_as_uint(m) | qs);
+                    }
+                }
+                // exclusive sums as S - a_k, the dominant edge's formed directly
+                float o = 0.0f;
+#pragma unroll
+                for (int k = 0; k < DMAX; k++)
+                    if (k < dc) o += (fabsf(av[k]) == amax) ? 0.0f : fabsf(av[k]);
+                const float sx = (amax > 0.5f * S) ? o : S - amax;
+#pragma unroll
+                for (int k = 0; k < DMAX; k++) {
+                    if (k < dc) {
+                        const float ak = fabsf(av[k]);
+                        const float mag = fminf(s_phi_out(ak == amax ? sx : S - ak), X);
+                        const float out =
+                            __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k]) ^ sg) & kSign));
+                        Rr[k * Z] = MsgT(out);
+                    }
+                }
+                pbad |= (par & kSign) != 0;
+            }
+            if (pbad) flags[tr & 1] = 1;
+            cluster.sync();
+            // ---------------- decision (the same in every CTA: all flags are read after the barrier)
+            bool any_bad = false;
+#pragma unroll
+            for (int k = 0; k < CLUSTER_CTAS; k++) any_bad |= cluster.map_shared_rank(flags, k)[tr & 1] != 0;
+            const bool conv = tr >= 1 && a.early_exit && !any_bad;
+            if (!conv) {
+                // ---------------- variable-node phase over the owned variables
+                for (int i = tid; i < n_var; i += nth) {
+                    const int jl = i / Z, c = i - jl * Z;
+                    const int j = col0 + jl;
+                    float sum = __ldg(L + j * Z + c);
+                    for (int e = t_colptr[j]; e < t_colptr[j + 1]; e++) {
+                        const int ce = t_cent[e];
+                        int rr = c - (ce >> 20);
+                        rr += (rr < 0) ? Z : 0;
+                        sum += (float)(t_cown[e] ? r_1 : r_0)[(ce & 0xfffff) + rr];
+                    }
+                    app[i] = sum + 0.0f;  // -0 -> +0: the sign bit is the decision
+                }
+                t++;
+            }
+            done = conv || t >= a.max_iter;
+            // the other flag was read by every CTA in the previous round (before this round's
+            // first barrier): clear it for the next round, which writes it after the barrier below
+            if (tid == 0) flags[(tr + 1) & 1] = 0;
+            cluster.sync();
+        }
+        // output: each CTA writes its variables
+        uint8_t *Bo = a.bits + cw * cd->N;
+        float *Ao = a.app_out ? a.app_out + cw * cd->N : nullptr;
+        for (int i = tid; i < n_var; i += nth) {
+            const float v = app[i];
+            Bo[col0 * Z + i] = v < 0.0f ? 1 : 0;
+            if (Ao) Ao[col0 * Z + i] = v;
+        }
+        if (q == 0 && tid == 0) a.iters[cw] = t;
+    }
+    cluster.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+
+// ------------------------------------------------------------------ host side
+
+// bytes of the table area ahead of APP (the kernel's layout)
+static size_t cl_tables_bytes() { return (16 + 4 * (2 * NNZ_MAX + MB_MAX + NB_MAX + 2 + NNZ_MAX) + 15) & ~(size_t)15; }
+
+// Split block rows and block columns between the cluster's CTAs, each at about an equal share
+// of the blocks; returns the largest per-CTA shared memory.
+static size_t cl_plan(const CodeDev &h, int msg, int *row_split, int *col_split)
+{
+    row_split[0] = col_split[0] = 0;
+    for (int q = 1; q < CLUSTER_CTAS; q++) {
+        const int want = (int)((int64_t)h.nnz * q / CLUSTER_CTAS);
+        int l = row_split[q - 1] + 1;
+        while (l < h.mb && h.rowptr[l] < want) l++;
+        int j = col_split[q - 1] + 1;
+        while (j < h.nb && h.colptr[j] < want) j++;
+        row_split[q] = l < h.mb ? l : h.mb - 1;
+        col_split[q] = j < h.nb ? j : h.nb - 1;
+    }
+    row_split[CLUSTER_CTAS] = h.mb;
+    col_split[CLUSTER_CTAS] = h.nb;
+    // the kernel places R after the largest posterior share in every CTA (one offset cluster-wide)
+    size_t napp = 0, nr = 0;
+    for (int q = 0; q < CLUSTER_CTAS; q++) {
+        const size_t na = (size_t)(col_split[q + 1] - col_split[q]) * h.Z;
+        const size_t nm = (size_t)(h.rowptr[row_split[q + 1]] - h.rowptr[row_split[q]]) * h.Z;
+        napp = na > napp ? na : napp;
+        nr = nm > nr ? nm : nr;
+    }
+    return cl_tables_bytes() + ((napp * 4 + 15) & ~(size_t)15) + nr * (msg == LDPC_MSG_F16 ? sizeof(__half) : sizeof(float));
+}
+
+int cluster_supported(const CodeDev &h, int msg)
+{
+    if (h.dc_max > 32 || h.mb < CLUSTER_CTAS || h.nb < CLUSTER_CTAS) return 0;
+    if ((int64_t)(h.nb / CLUSTER_CTAS + 1) * h.Z >= (1 << 19) || (int64_t)h.E >= (1 << 20))
+        return 0;  // the packed table fields (posterior and message bases)
+    int rs[CLUSTER_CTAS + 1], cs[CLUSTER_CTAS + 1];
+    const size_t need = cl_plan(h, msg, rs, cs);
+    int dev = 0, lim = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return need <= (size_t)(lim > 0 ? lim : 227 * 1024);
+}
+
+template <int DMAX, typename MsgT>
+static cudaError_t launch_cluster(const ClusterArgs &a, size_t smem, int64_t n_cw, const CodeDev *d, cudaStream_t s)
+{
+    cudaError_t e = ensure_smem<k_flood_cluster<DMAX, MsgT>>(smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CLUSTER_CTAS, 1, 1);
+    cfg.blockDim = dim3(cl_threads<DMAX>(), 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, k_flood_cluster<DMAX, MsgT>, &cfg);
+    if (e != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        int dev = 0, nsm = 2;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        clusters = nsm / CLUSTER_CTAS;
+    }
+    if ((int64_t)clusters > n_cw) clusters = (int)n_cw;
+    LaunchScope ls(F_SLOTS, s);
+    k_flood_cluster<DMAX, MsgT><<<(unsigned)(clusters * CLUSTER_CTAS), cl_threads<DMAX>(), smem, s>>>(d, a);
+    return cudaGetLastError();
+}
+
+cudaError_t flood_cluster_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p, const float *llr,
+                                 int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out, void *counter,
+                                 cudaStream_t s)
+{
+    ClusterArgs a;
+    memset(&a, 0, sizeof a);
+    const size_t smem = cl_plan(h, p.msg, a.row_split, a.col_split);
+    a.llr = llr;
+    a.bits = bits;
+    a.iters = iters;
+    a.app_out = app_out;
+    a.n_cw = n_cw;
+    a.next = static_cast<unsigned long long *>(counter);
+    a.max_iter = p.max_iter;
+    a.early_exit = p.early_exit;
+    a.X = p.phi_clamp;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const bool f16 = p.msg == LDPC_MSG_F16;
+    if (h.dc_max <= 8)
+        return f16 ? launch_cluster<8, __half>(a, smem, n_cw, d, s) : launch_cluster<8, float>(a, smem, n_cw, d, s);
+    if (h.dc_max <= 16)
+        return f16 ? launch_cluster<16, __half>(a, smem, n_cw, d, s) : launch_cluster<16, float>(a, smem, n_cw, d, s);
+    return f16 ? launch_cluster<32, __half>(a, smem, n_cw, d, s) : launch_cluster<32, float>(a, smem, n_cw, d, s);
+}
+
+}  // namespace ldpc

@@ -254,7 +254,8 @@ static ldpc_status check_params(const ldpc_code *c, const ldpc_decode_params *p,
     if (p->early_exit != 0 && p->early_exit != 1) return fail(LDPC_EINVAL, "early_exit must be 0 or 1");
     for (int i = 0; i < 4; i++)
         if (p->reserved[i] != 0) return fail(LDPC_EINVAL, "reserved fields must be zero");
-    if (p->impl != LDPC_IMPL_AUTO && p->impl != LDPC_IMPL_PLAIN && p->impl != LDPC_IMPL_STREAMING)
+    if (p->impl != LDPC_IMPL_AUTO && p->impl != LDPC_IMPL_PLAIN && p->impl != LDPC_IMPL_STREAMING &&
+        p->impl != LDPC_IMPL_CLUSTER)
         return fail(LDPC_EINVAL, "bad impl");
     if (p->sched == LDPC_SCHED_FLOODING && p->algo == LDPC_ALGO_SPA) {
         if (p->msg != LDPC_MSG_F32 && p->msg != LDPC_MSG_F16)
@@ -264,6 +265,8 @@ static ldpc_status check_params(const ldpc_code *c, const ldpc_decode_params *p,
         if (llr_type != LDPC_LLR_F32) return fail(LDPC_EINVAL, "flooding SPA takes fp32 LLRs");
         if (p->impl == LDPC_IMPL_PLAIN && p->msg != LDPC_MSG_F32)
             return fail(LDPC_ENOTSUP, "the plain comparator stores F32 messages");
+        if (p->impl == LDPC_IMPL_CLUSTER && !ldpc::cluster_supported(c->host, p->msg))
+            return fail(LDPC_ENOTSUP, "code does not fit the cluster decoder");
         if (c->host.dc_max > 32) return fail(LDPC_ENOTSUP, "check degree %d > 32", c->host.dc_max);
         return LDPC_OK;
     }
@@ -281,7 +284,8 @@ static ldpc_status check_params(const ldpc_code *c, const ldpc_decode_params *p,
     }
     if (p->sched == LDPC_SCHED_LAYERED && p->algo == LDPC_ALGO_NMS) {
         if (p->msg != LDPC_MSG_I8) return fail(LDPC_ENOTSUP, "layered min-sum stores I8 messages");
-        if (p->impl == LDPC_IMPL_PLAIN) return fail(LDPC_ENOTSUP, "no plain layered implementation");
+        if (p->impl == LDPC_IMPL_PLAIN || p->impl == LDPC_IMPL_CLUSTER)
+            return fail(LDPC_ENOTSUP, "layered min-sum runs on the slot decoders");
         if (p->msg_sat < 1 || p->msg_sat > 127 || p->app_sat < p->msg_sat || p->app_sat > 127)
             return fail(LDPC_EINVAL, "need 1 <= msg_sat <= app_sat <= 127");
         if (p->nms_alpha_num < 1 || p->nms_alpha_shift < 0 || p->nms_alpha_shift > 16 ||
@@ -306,6 +310,16 @@ static bool use_slots(const ldpc_code *c, const ldpc_decode_params *p)
            c->tuned_flood[p->msg == LDPC_MSG_F16 ? 1 : 0] != SCHED_STREAMING;
 }
 
+// The cluster decoder serves flooding codes whose codeword does not fit one CTA (AUTO), or
+// any code that fits its split when asked for.
+static bool use_cluster(const ldpc_code *c, const ldpc_decode_params *p)
+{
+    if (p->sched != LDPC_SCHED_FLOODING) return false;
+    if (p->impl == LDPC_IMPL_CLUSTER) return true;
+    return p->impl == LDPC_IMPL_AUTO && !ldpc::slots_supported(c->host, p->msg) &&
+           ldpc::cluster_supported(c->host, p->msg) && c->tuned_flood[p->msg == LDPC_MSG_F16 ? 1 : 0] != SCHED_STREAMING;
+}
+
 // The layered min-sum runs as persistent slots (work counter in the workspace) unless
 // LDPC_IMPL_STREAMING asks for the one-CTA-per-group kernel, which needs no workspace.
 static bool use_layered_slots(const ldpc_code *c, const ldpc_decode_params *p)
@@ -324,7 +338,7 @@ static bool use_layered_spa(const ldpc_decode_params *p)
 static size_t ws_bytes(const ldpc_code *c, const ldpc_decode_params *p, int64_t n_cw)
 {
     if (n_cw == 0) return 0;
-    if (use_layered_slots(c, p) || use_layered_spa(p)) return ldpc::SLOTS_WS_BYTES;
+    if (use_layered_slots(c, p) || use_layered_spa(p) || use_cluster(c, p)) return ldpc::SLOTS_WS_BYTES;
     if (p->sched == LDPC_SCHED_LAYERED) return 0;
     if (use_slots(c, p)) return ldpc::SLOTS_WS_BYTES;
     return ldpc::flood_ws_layout(c->host, n_cw, p->msg, nullptr, nullptr);
@@ -379,6 +393,9 @@ ldpc_status ldpc_decode_batch(const ldpc_code *c, const ldpc_decode_params *p, c
     } else if (use_slots(c, p)) {
         const ldpc::HostReq rq = {c, llr, n_cw, bits, iters, app};
         e = ldpc::flood_multi_decode(&rq, 1, *p, ws, s);
+    } else if (use_cluster(c, p)) {
+        e = ldpc::flood_cluster_decode(c->host, c->dev, *p, static_cast<const float *>(llr), n_cw, bits, iters, app,
+                                       ws, s);
     } else {
         ldpc::FloodWs w;
         ldpc::flood_ws_layout(c->host, n_cw, p->msg, &w, static_cast<char *>(ws));
@@ -474,6 +491,8 @@ ldpc_status ldpc_autotune(ldpc_code *c, const ldpc_decode_params *p, const void 
         if (ldpc::slots_supported(c->host, p->msg)) {
             cand[nc++] = SCHED_SLOTS_V1;
             if (ldpc::slots_pairable(c->host, p->msg)) cand[nc++] = SCHED_SLOTS_V2;
+        } else if (ldpc::cluster_supported(c->host, p->msg)) {
+            cand[nc++] = SCHED_SLOTS_V1;  // the cluster decoder
         }
     } else if (ldpc::layered_slots_per_cta(c->host) > 0) {
         cand[nc++] = SCHED_SLOTS_V1;

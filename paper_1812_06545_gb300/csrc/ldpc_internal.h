@@ -123,6 +123,13 @@ cudaError_t layered_spa_decode(const CodeDev &host, const CodeDev *dev, const ld
                                int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out, void *counter,
                                cudaStream_t s);
 
+// Flooding SPA cluster decoder (flood_cluster.cu): one codeword per two-SM cluster, for codes
+// whose codeword does not fit one CTA.
+int cluster_supported(const CodeDev &host, int msg);
+cudaError_t flood_cluster_decode(const CodeDev &host, const CodeDev *dev, const ldpc_decode_params &p, const float *llr,
+                                 int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out, void *counter,
+                                 cudaStream_t s);
+
 // Flooding SPA slot decoder: supported when one codeword of the code fits a CTA.
 int slots_supported(const CodeDev &host, int msg);
 int slots_pairable(const CodeDev &host, int msg);

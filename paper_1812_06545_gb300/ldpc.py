@@ -22,7 +22,7 @@ LDPC_SCHED_FLOODING, LDPC_SCHED_LAYERED = 0, 1
 LDPC_ALGO_SPA, LDPC_ALGO_NMS = 0, 1
 LDPC_MSG_F32, LDPC_MSG_F16, LDPC_MSG_I8 = 0, 1, 2
 LDPC_LLR_F32, LDPC_LLR_I8 = 0, 1
-LDPC_IMPL_AUTO, LDPC_IMPL_PLAIN, LDPC_IMPL_STREAMING = 0, 1, 2
+LDPC_IMPL_AUTO, LDPC_IMPL_PLAIN, LDPC_IMPL_STREAMING, LDPC_IMPL_CLUSTER = 0, 1, 2, 3
 FAMILIES = {"interleave": 0, "check_node": 1, "variable_node": 2, "deinterleave": 3, "layered": 4,
             "plain_check_node": 5, "plain_variable_node": 6, "slots": 7, "layered_spa": 8}
 
@@ -364,6 +364,8 @@ FORMS = {
     "plain_f32": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F32, impl=LDPC_IMPL_PLAIN),
     "stream_f32": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F32, impl=LDPC_IMPL_STREAMING),
     "stream_f16": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F16, impl=LDPC_IMPL_STREAMING),
+    "cluster_f32": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F32, impl=LDPC_IMPL_CLUSTER),
+    "cluster_f16": dict(sched=LDPC_SCHED_FLOODING, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F16, impl=LDPC_IMPL_CLUSTER),
     "layered_f32": dict(sched=LDPC_SCHED_LAYERED, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F32),
     "layered_f16": dict(sched=LDPC_SCHED_LAYERED, algo=LDPC_ALGO_SPA, msg=LDPC_MSG_F16),
     "layered_i8": dict(sched=LDPC_SCHED_LAYERED, algo=LDPC_ALGO_NMS, msg=LDPC_MSG_I8),
