@@ -37,7 +37,10 @@ struct ClusterArgs {
     int64_t n_cw;
     unsigned long long *next;
     int row_split[CLUSTER_CTAS + 1];  // block rows [row_split[q], row_split[q+1]) belong to CTA q
-    int col_split[CLUSTER_CTAS + 1];  // block columns likewise
+    int ncols[CLUSTER_CTAS];          // block columns CTA q holds the posteriors of
+    int col_owner[NB_MAX];            // owner of block column j
+    int col_slot[NB_MAX];             // its place among the owner's columns
+    int col_list[CLUSTER_CTAS][NB_MAX];  // CTA q's columns in place order
     int max_iter, early_exit;
     float X;
 };
@@ -47,6 +50,86 @@ __host__ __device__ inline int cl_owner(const int *split, int x)
     int q = 0;
     while (q < CLUSTER_CTAS - 1 && x >= split[q + 1]) q++;
     return q;
+}
+
+// One check of an owned row: Q = APP - R over its edges (posteriors wherever they live), the
+// phi rule, messages written in place; returns the parity of the posteriors' sign bits.
+template <int D, bool EXACT, typename MsgT>
+__device__ __forceinline__ uint32_t cl_check(int dc, const int32_t *__restrict__ ent, MsgT *Rr, const float *app_0,
+                                             const float *app_1, int r, int Z, float X, float Xb)
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    float av[D];
+    uint32_t sg = 0, par = 0;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        if (EXACT || k < dc) {
+            const int e = ent[k];
+            int x = r + (e >> 20);
+            x -= (x >= Z) ? Z : 0;
+            const float ap = ((e >> 19) & 1 ? app_1 : app_0)[(e & 0x7ffff) + x];
+            const float qv = ap - (float)Rr[k * Z];
+            par ^= __float_as_uint(ap);
+            const uint32_t qs = __float_as_uint(qv) & kSign;
+            sg ^= qs;
+            av[k] = __uint_as_float(__float_as_uint(fminf(s_psi_in(fminf(fabsf(qv), X)), Xb)) | qs);
+        }
+    }
+    if constexpr (D <= 8) {
+        // exclusive sums from suffix and prefix sums (no cancellation)
+        float sf[D + 1];
+        sf[D] = 0.0f;
+#pragma unroll
+        for (int k = D - 1; k >= 0; k--) sf[k] = (EXACT || k < dc) ? sf[k + 1] + fabsf(av[k]) : 0.0f;
+        float pre = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            if (EXACT || k < dc) {
+                const float mag = fminf(s_phi_out(pre + sf[k + 1]), X);
+                pre += fabsf(av[k]);
+                Rr[k * Z] = MsgT(__uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k]) ^ sg) & kSign)));
+            }
+        }
+    } else {
+        // S - a_k, the dominant edge's sum formed directly
+        float S = 0.0f, amax = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; k++)
+            if (EXACT || k < dc) {
+                S += fabsf(av[k]);
+                amax = fmaxf(amax, fabsf(av[k]));
+            }
+        float o = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; k++)
+            if (EXACT || k < dc) o += (fabsf(av[k]) == amax) ? 0.0f : fabsf(av[k]);
+        const float sx = (amax > 0.5f * S) ? o : S - amax;
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            if (EXACT || k < dc) {
+                const float ak = fabsf(av[k]);
+                const float mag = fminf(s_phi_out(ak == amax ? sx : S - ak), X);
+                Rr[k * Z] = MsgT(__uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k]) ^ sg) & kSign)));
+            }
+        }
+    }
+    return par;
+}
+
+template <int D, int DMAX, typename MsgT>
+__device__ __forceinline__ uint32_t cl_check_dispatch(int dc, const int32_t *__restrict__ ent, MsgT *Rr,
+                                                      const float *app_0, const float *app_1, int r, int Z, float X,
+                                                      float Xb)
+{
+    if constexpr (D >= DMAX) {
+        return cl_check<DMAX, false, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
+    } else if constexpr (D <= 8) {
+        if (dc == D) return cl_check<D, true, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
+        return cl_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
+    } else {
+        if (dc <= D) return cl_check<D, false, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
+        return cl_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
+    }
 }
 
 // threads per CTA: higher check degrees keep more values live per thread
@@ -73,7 +156,6 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
     int32_t *t_colptr = t_ent + NNZ_MAX;                          // [nb + 1]
     int32_t *t_cent = t_colptr + NB_MAX + 1;                      // [nnz] (shift << 20) | owner R base
     int32_t *t_cown = t_cent + NNZ_MAX;                           // [nnz] owner of the entry's row
-    const int col0 = a.col_split[q], col1 = a.col_split[q + 1];
     const int row0 = a.row_split[q], row1 = a.row_split[q + 1];
     // block b's owner of posteriors and its base there; column entry's owner of messages
     for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
@@ -83,8 +165,7 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
     for (int b = tid; b < nnz; b += nth) {
         const int e = cd->ent[b];
         const int j = e >> 16, s = e & 0xffff;
-        const int qo = cl_owner(a.col_split, j);
-        t_ent[b] = (s << 20) | (qo << 19) | ((j - a.col_split[qo]) * Z);
+        t_ent[b] = (s << 20) | (a.col_owner[j] << 19) | (a.col_slot[j] * Z);
     }
     for (int i = tid; i < nnz; i += nth) {
         const int ce = cd->colent[i];
@@ -101,17 +182,15 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
     // mapping an address into another CTA of the cluster finds that CTA's messages
     int napp_max = 0;
 #pragma unroll
-    for (int k = 0; k < CLUSTER_CTAS; k++) {
-        const int na = (a.col_split[k + 1] - a.col_split[k]) * Z;
-        napp_max = na > napp_max ? na : napp_max;
-    }
+    for (int k = 0; k < CLUSTER_CTAS; k++) napp_max = a.ncols[k] * Z > napp_max ? a.ncols[k] * Z : napp_max;
     MsgT *R = reinterpret_cast<MsgT *>(smem + off_app + (((size_t)napp_max * 4 + 15) & ~(size_t)15));
     // the cluster's posterior and message arrays, by owning CTA (generic pointers; the own
     // CTA's are plain shared memory)
     static_assert(CLUSTER_CTAS == 2, "the owner selects below assume two CTAs");
     const float *app_0 = cluster.map_shared_rank(app, 0), *app_1 = cluster.map_shared_rank(app, 1);
     const MsgT *r_0 = cluster.map_shared_rank(R, 0), *r_1 = cluster.map_shared_rank(R, 1);
-    const int n_check = (row1 - row0) * Z, n_var = (col1 - col0) * Z;
+    const int n_check = (row1 - row0) * Z, n_var = a.ncols[q] * Z;
+    const int *my_cols = a.col_list[q];
     int64_t *cw0 = cluster.map_shared_rank(cwp, 0);
     cluster.sync();  // tables built in every CTA before any remote access
 
@@ -128,7 +207,8 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
         // load: APP = L (+0: no -0) for owned variables, R = 0 for owned edges
         const float *L = a.llr + cw * cd->N;
         for (int i = tid; i < n_var; i += nth) {
-            const float v = __ldg(L + col0 * Z + i);
+            const int jl = i / Z, c = i - jl * Z;
+            const float v = __ldg(L + my_cols[jl] * Z + c);
             if (!isfinite(v)) atomicOr(cd->status, IN_NONFINITE);
             app[i] = v + 0.0f;
         }
@@ -143,45 +223,10 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
             for (int w = tid; w < n_check; w += nth) {
                 const int lr = w / Z, r = w - lr * Z;
                 const int l = row0 + lr;
-                const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
-                MsgT *Rr = R + (b0 - blk0) * Z + r;
-                float av[DMAX];
-                uint32_t sg = 0, par = 0;
-                float S = 0.0f, amax = 0.0f;
-#pragma unroll
-                for (int k = 0; k < DMAX; k++) {
-                    if (k < dc) {
-                        const int e = t_ent[b0 + k];
-                        int x = r + (e >> 20);
-                        x -= (x >= Z) ? Z : 0;
-                        const float ap = ((e >> 19) & 1 ? app_1 : app_0)[(e & 0x7ffff) + x];
-                        const float rv = (float)Rr[k * Z];
-                        const float qv = ap - rv;
-                        par ^= __float_as_uint(ap);
-                        const float m = fminf(s_psi_in(fminf(fabsf(qv), X)), Xb);
-                        const uint32_t qs = __float_as_uint(qv) & kSign;
-                        sg ^= qs;
-                        S += m;
-                        amax = fmaxf(amax, m);
-                        av[k] = __uint_as_float(__float_as_uint(m) | qs);
-                    }
-                }
-                // exclusive sums as S - a_k, the dominant edge's formed directly
-                float o = 0.0f;
-#pragma unroll
-                for (int k = 0; k < DMAX; k++)
-                    if (k < dc) o += (fabsf(av[k]) == amax) ? 0.0f : fabsf(av[k]);
-                const float sx = (amax > 0.5f * S) ? o : S - amax;
-#pragma unroll
-                for (int k = 0; k < DMAX; k++) {
-                    if (k < dc) {
-                        const float ak = fabsf(av[k]);
-                        const float mag = fminf(s_phi_out(ak == amax ? sx : S - ak), X);
-                        const float out =
-                            __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k]) ^ sg) & kSign));
-                        Rr[k * Z] = MsgT(out);
-                    }
-                }
+                const int b0 = t_rowptr[l];
+                const uint32_t par = cl_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ent + b0,
+                                                                      R + (b0 - blk0) * Z + r, app_0, app_1, r, Z,
+                                                                      X, Xb);
                 pbad |= (par & kSign) != 0;
             }
             if (pbad) flags[tr & 1] = 1;
@@ -195,7 +240,7 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
                 // ---------------- variable-node phase over the owned variables
                 for (int i = tid; i < n_var; i += nth) {
                     const int jl = i / Z, c = i - jl * Z;
-                    const int j = col0 + jl;
+                    const int j = my_cols[jl];
                     float sum = __ldg(L + j * Z + c);
                     for (int e = t_colptr[j]; e < t_colptr[j + 1]; e++) {
                         const int ce = t_cent[e];
@@ -217,9 +262,11 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
         uint8_t *Bo = a.bits + cw * cd->N;
         float *Ao = a.app_out ? a.app_out + cw * cd->N : nullptr;
         for (int i = tid; i < n_var; i += nth) {
+            const int jl = i / Z, c = i - jl * Z;
+            const int n = my_cols[jl] * Z + c;
             const float v = app[i];
-            Bo[col0 * Z + i] = v < 0.0f ? 1 : 0;
-            if (Ao) Ao[col0 * Z + i] = v;
+            Bo[n] = v < 0.0f ? 1 : 0;
+            if (Ao) Ao[n] = v;
         }
         if (q == 0 && tid == 0) a.iters[cw] = t;
     }
@@ -232,44 +279,90 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
 // bytes of the table area ahead of APP (the kernel's layout)
 static size_t cl_tables_bytes() { return (16 + 4 * (2 * NNZ_MAX + MB_MAX + NB_MAX + 2 + NNZ_MAX) + 15) & ~(size_t)15; }
 
-// Split block rows and block columns between the cluster's CTAs, each at about an equal share
-// of the blocks; returns the largest per-CTA shared memory.
-static size_t cl_plan(const CodeDev &h, int msg, int *row_split, int *col_split)
+// Split the block rows between the cluster's CTAs in contiguous ranges of about equal block
+// counts, then give each block column to the CTA that owns most of its blocks' rows (its
+// posteriors are then read locally by most of its checks), moving the least attached columns
+// while a CTA would need more shared memory than the largest allowed.  Returns the per-CTA
+// shared memory (the same layout in every CTA), or 0 if no assignment fits.
+static size_t cl_plan(const CodeDev &h, int msg, ClusterArgs &a, size_t limit)
 {
-    row_split[0] = col_split[0] = 0;
+    a.row_split[0] = 0;
     for (int q = 1; q < CLUSTER_CTAS; q++) {
         const int want = (int)((int64_t)h.nnz * q / CLUSTER_CTAS);
-        int l = row_split[q - 1] + 1;
+        int l = a.row_split[q - 1] + 1;
         while (l < h.mb && h.rowptr[l] < want) l++;
-        int j = col_split[q - 1] + 1;
-        while (j < h.nb && h.colptr[j] < want) j++;
-        row_split[q] = l < h.mb ? l : h.mb - 1;
-        col_split[q] = j < h.nb ? j : h.nb - 1;
+        a.row_split[q] = l < h.mb ? l : h.mb - 1;
     }
-    row_split[CLUSTER_CTAS] = h.mb;
-    col_split[CLUSTER_CTAS] = h.nb;
-    // the kernel places R after the largest posterior share in every CTA (one offset cluster-wide)
-    size_t napp = 0, nr = 0;
+    a.row_split[CLUSTER_CTAS] = h.mb;
+    const size_t msz = msg == LDPC_MSG_F16 ? sizeof(__half) : sizeof(float);
+    size_t nr = 0;
     for (int q = 0; q < CLUSTER_CTAS; q++) {
-        const size_t na = (size_t)(col_split[q + 1] - col_split[q]) * h.Z;
-        const size_t nm = (size_t)(h.rowptr[row_split[q + 1]] - h.rowptr[row_split[q]]) * h.Z;
-        napp = na > napp ? na : napp;
+        const size_t nm = (size_t)(h.rowptr[a.row_split[q + 1]] - h.rowptr[a.row_split[q]]) * h.Z;
         nr = nm > nr ? nm : nr;
     }
-    return cl_tables_bytes() + ((napp * 4 + 15) & ~(size_t)15) + nr * (msg == LDPC_MSG_F16 ? sizeof(__half) : sizeof(float));
+    // affinity of column j to CTA q: its blocks in q's rows
+    int aff[NB_MAX][CLUSTER_CTAS] = {};
+    for (int j = 0; j < h.nb; j++)
+        for (int i = h.colptr[j]; i < h.colptr[j + 1]; i++) {
+            const int b = h.colent[i] >> 16;
+            int l = 0;
+            while (l < h.mb - 1 && b >= h.rowptr[l + 1]) l++;
+            aff[j][cl_owner(a.row_split, l)]++;
+        }
+    int cnt[CLUSTER_CTAS] = {};
+    for (int j = 0; j < h.nb; j++) {
+        int best = 0;
+        for (int q = 1; q < CLUSTER_CTAS; q++)
+            if (aff[j][q] > aff[j][best] || (aff[j][q] == aff[j][best] && cnt[q] < cnt[best])) best = q;
+        a.col_owner[j] = best;
+        cnt[best]++;
+    }
+    // the posterior share of a CTA may not exceed what its shared memory has left
+    const size_t fixed = cl_tables_bytes() + nr * msz;
+    const int cap = limit > fixed ? (int)((limit - fixed) / (4 * (size_t)h.Z)) : 0;
+    for (int q = 0; q < CLUSTER_CTAS; q++) {
+        while (cnt[q] > cap) {
+            // move q's column with the least attachment to q to the CTA with the most room
+            int jm = -1;
+            for (int j = 0; j < h.nb; j++)
+                if (a.col_owner[j] == q && (jm < 0 || aff[j][q] < aff[jm][q])) jm = j;
+            int to = -1;
+            for (int k = 0; k < CLUSTER_CTAS; k++)
+                if (k != q && cnt[k] < cap && (to < 0 || cnt[k] < cnt[to])) to = k;
+            if (jm < 0 || to < 0) return 0;
+            a.col_owner[jm] = to;
+            cnt[q]--;
+            cnt[to]++;
+        }
+    }
+    for (int q = 0; q < CLUSTER_CTAS; q++) a.ncols[q] = 0;
+    for (int j = 0; j < h.nb; j++) {
+        const int q = a.col_owner[j];
+        a.col_slot[j] = a.ncols[q];
+        a.col_list[q][a.ncols[q]++] = j;
+    }
+    int nmax = 0;
+    for (int q = 0; q < CLUSTER_CTAS; q++) nmax = a.ncols[q] > nmax ? a.ncols[q] : nmax;
+    return cl_tables_bytes() + (((size_t)nmax * h.Z * 4 + 15) & ~(size_t)15) + nr * msz;
+}
+
+static size_t cl_limit()
+{
+    int dev = 0, lim = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return lim > 0 ? (size_t)lim : 227 * 1024;
 }
 
 int cluster_supported(const CodeDev &h, int msg)
 {
     if (h.dc_max > 32 || h.mb < CLUSTER_CTAS || h.nb < CLUSTER_CTAS) return 0;
-    if ((int64_t)(h.nb / CLUSTER_CTAS + 1) * h.Z >= (1 << 19) || (int64_t)h.E >= (1 << 20))
+    if ((int64_t)h.N >= (1 << 19) || (int64_t)h.E >= (1 << 20))
         return 0;  // the packed table fields (posterior and message bases)
-    int rs[CLUSTER_CTAS + 1], cs[CLUSTER_CTAS + 1];
-    const size_t need = cl_plan(h, msg, rs, cs);
-    int dev = 0, lim = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return need <= (size_t)(lim > 0 ? lim : 227 * 1024);
+    ClusterArgs a;
+    memset(&a, 0, sizeof a);
+    const size_t need = cl_plan(h, msg, a, cl_limit());
+    return need > 0 && need <= cl_limit();
 }
 
 template <int DMAX, typename MsgT>
@@ -303,7 +396,8 @@ cudaError_t flood_cluster_decode(const CodeDev &h, const CodeDev *d, const ldpc_
 {
     ClusterArgs a;
     memset(&a, 0, sizeof a);
-    const size_t smem = cl_plan(h, p.msg, a.row_split, a.col_split);
+    const size_t smem = cl_plan(h, p.msg, a, cl_limit());
+    if (smem == 0) return cudaErrorInvalidValue;
     a.llr = llr;
     a.bits = bits;
     a.iters = iters;
