@@ -167,14 +167,15 @@ typedef struct {
  * theirs runs dry, and a codeword's slot is refilled the moment it converges.  A codeword
  * decodes to exactly the same result as in ldpc_decode_batch (alone or in any mix).
  *   reqs       host array of n_req <= 128 requests over <= 16 distinct codes, all decoded
- *              with the same params (impl must be AUTO; every code must fit the on-chip
- *              slot decoder of the form - ldpc_decode_batch with LDPC_IMPL_STREAMING serves
- *              larger codes).
+ *              with the same params (impl must be AUTO; every code must fit the form's
+ *              on-chip decoders: a slot of one CTA, or for flooding a two-SM cluster -
+ *              ldpc_decode_batch with LDPC_IMPL_STREAMING serves larger codes).
  *   llr_type   applies to every request.
  *   workspace  >= ldpc_multi_workspace_size() bytes of device memory (work counters),
  *              256-byte aligned, or NULL for a stream-ordered allocation on `stream`.
- * The flooding forms run all requests in one launch; the layered form issues one persistent
- * launch per request on `stream`. */
+ * The flooding forms run all slot-sized requests in one launch and each cluster-sized
+ * request in a launch of its own; the layered forms issue one persistent launch per request
+ * on `stream`. */
 ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldpc_decode_params *p,
                               int32_t llr_type, void *workspace, size_t workspace_bytes, void *stream);
 

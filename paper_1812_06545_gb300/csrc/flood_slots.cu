@@ -410,6 +410,15 @@ cudaError_t flood_multi_decode(const HostReq *reqs, int n, const ldpc_decode_par
         gd.code = codes[g]->dev;
         gd.C = slots_for(h, p.msg, V, tbl, limit);
         if (gd.C < V) return cudaErrorInvalidValue;
+        {
+            // a small batch spreads over the SMs rather than filling a few CTAs' slots
+            int64_t items = 0;
+            for (int i = 0; i < n; i++)
+                if (reqs[i].n_cw > 0 && reqs[i].code == codes[g]) items += reqs[i].n_cw;
+            int64_t cap = (items + sm_count() - 1) / sm_count();
+            cap = ((cap + V - 1) / V) * V;
+            if (cap < gd.C) gd.C = (int)cap;
+        }
         gd.N = h.N;
         gd.E = h.E;
         gd.Z = h.Z;

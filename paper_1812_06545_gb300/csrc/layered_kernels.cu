@@ -409,12 +409,13 @@ static size_t lslots_smem(const CodeDev &h, int C)
 struct LslotShape {
     int C, K, TPG;
 };
-static LslotShape lslots_shape(const CodeDev &h)
+static LslotShape lslots_shape(const CodeDev &h, int64_t cap = SLOTS_MAX)
 {
     LslotShape best = {0, 1, 32};
     if (h.dc_max > 32 || h.N >= 65536) return best;
     int cmax = SLOTS_MAX;
     while (cmax > 0 && lslots_smem(h, cmax) > 200 * 1024) cmax--;
+    if (cap >= 1 && cap < cmax) cmax = (int)cap;  // a small batch spreads over the SMs
     for (int K = 1; K <= cmax; K++) {
         const int tpg = ((K * h.Z + 31) / 32) * 32;
         int G = 1024 / tpg;
@@ -455,7 +456,10 @@ cudaError_t layered_slots_decode(const CodeDev &h, const CodeDev *d, const ldpc_
     a.llr_type = llr_type;
     a.scale = p.llr_scale;
     a.n_cw = n_cw;
-    const LslotShape sh = lslots_shape(h);
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const LslotShape sh = lslots_shape(h, (n_cw + nsm - 1) / nsm);
     a.C = sh.C;
     if (a.C < 1) return cudaErrorInvalidValue;
     a.K = sh.K;

@@ -344,7 +344,7 @@ static size_t lspa_smem(const CodeDev &h, int msg, int C)
 struct LspaShape {
     int C, K, TPG;
 };
-static LspaShape lspa_shape(const CodeDev &h, int msg)
+static LspaShape lspa_shape(const CodeDev &h, int msg, int64_t cap = SLOTS_MAX)
 {
     LspaShape best = {0, 1, 32};
     if (h.dc_max > 32 || h.N >= 65536) return best;
@@ -354,6 +354,7 @@ static LspaShape lspa_shape(const CodeDev &h, int msg)
     const size_t limit = lim > 0 ? (size_t)lim : 227 * 1024;
     int cmax = SLOTS_MAX;
     while (cmax > 0 && lspa_smem(h, msg, cmax) > limit) cmax--;
+    if (cap >= 1 && cap < cmax) cmax = (int)cap;  // a small batch spreads over the SMs
     const int tmax = lspa_threads_for(h.dc_max, msg);
     for (int K = 1; K <= cmax; K++) {
         const int tpg = ((K * h.Z + 31) / 32) * 32;
@@ -402,7 +403,10 @@ cudaError_t layered_spa_decode(const CodeDev &h, const CodeDev *d, const ldpc_de
     LayeredSpaArgs a;
     a.llr = llr;
     a.n_cw = n_cw;
-    const LspaShape sh = lspa_shape(h, p.msg);
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const LspaShape sh = lspa_shape(h, p.msg, (n_cw + nsm - 1) / nsm);
     a.C = sh.C;
     if (a.C < 1) return cudaErrorInvalidValue;
     a.K = sh.K;

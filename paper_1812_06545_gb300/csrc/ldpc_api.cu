@@ -425,7 +425,7 @@ ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldp
         if (q.n_cw < 0 || q.n_cw > ((int64_t)1 << 31)) return fail(LDPC_EINVAL, "request %d: bad n_cw", i);
         if (q.n_cw > 0 && (!q.llr_dev || !q.bits_dev || !q.iters_dev))
             return fail(LDPC_EINVAL, "request %d: llr, bits and iters must be non-NULL", i);
-        const bool fits = p->sched == LDPC_SCHED_FLOODING ? use_slots(q.code, p)
+        const bool fits = p->sched == LDPC_SCHED_FLOODING ? (use_slots(q.code, p) || use_cluster(q.code, p))
                           : use_layered_spa(p)               ? true
                                                              : use_layered_slots(q.code, p);
         if (!fits) return fail(LDPC_ENOTSUP, "request %d: code too large for the slot decoders", i);
@@ -457,7 +457,18 @@ ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldp
         own = true;
     }
     if (p->sched == LDPC_SCHED_FLOODING) {
-        e = ldpc::flood_multi_decode(hr, n_req, *p, ws, s);
+        // slot-sized codes share one persistent launch; a code that needs a cluster per
+        // codeword gets its own cluster launch (stream-ordered: the work counter is reused)
+        ldpc::HostReq small[ldpc::MULTI_MAX_REQS];
+        int ns = 0;
+        for (int i = 0; i < n_req; i++)
+            if (hr[i].n_cw > 0 && use_slots(hr[i].code, p)) small[ns++] = hr[i];
+        e = ns ? ldpc::flood_multi_decode(small, ns, *p, ws, s) : cudaSuccess;
+        for (int i = 0; i < n_req && e == cudaSuccess; i++)
+            if (hr[i].n_cw > 0 && !use_slots(hr[i].code, p))
+                e = ldpc::flood_cluster_decode(hr[i].code->host, hr[i].code->dev, *p,
+                                               static_cast<const float *>(hr[i].llr), hr[i].n_cw, hr[i].bits,
+                                               hr[i].iters, hr[i].app, ws, s);
     } else {
         e = cudaSuccess;
         for (int i = 0; i < n_req && e == cudaSuccess; i++)

@@ -83,13 +83,27 @@ def test_mixed_launch_argument_errors(cuda_dev):
     with pytest.raises(ldpc.LdpcError) as ei:
         ldpc.ldpc_decode_multi([(code.handle, x, 4, o[0], o[1], None)], ldpc.params_for("stream_f32"))
     assert ei.value.status == ldpc.LDPC_ENOTSUP
-    B, Z = I.load_code("qc34x68_z384_s5")
-    big = ldpc.Code(B, Z)
-    xb = torch.zeros((1, big.N), device=cuda_dev)
-    ob = outputs(big, 1, cuda_dev)
-    with pytest.raises(ldpc.LdpcError) as ei:
-        ldpc.ldpc_decode_multi([(big.handle, xb, 1, ob[0], ob[1], None)], ldpc.params_for("flood_f32"))
-    assert ei.value.status == ldpc.LDPC_ENOTSUP
     with pytest.raises(ldpc.LdpcError):
         ldpc.ldpc_decode_multi([(code.handle, x, 4, None, o[1], None)], ldpc.params_for("flood_f32"))
     ldpc.ldpc_decode_multi([], ldpc.params_for("flood_f32"))
+
+
+def test_mixed_launch_with_a_cluster_sized_code(cuda_dev):
+    # a code whose codeword exceeds one SM joins a mixed launch: it runs on the cluster
+    # decoder in a launch of its own, the others in the shared persistent launch; every
+    # request decodes exactly as alone
+    p = ldpc.params_for("flood_f16", max_iter=20)
+    names = [FAMILY[0], "qc34x68_z384_s5", FAMILY[5]]
+    reqs, outs, refs = [], [], []
+    for k, name in enumerate(names):
+        code = gpu_code(name)
+        _, _, c, L = I.make_frames(name, 37 + 11 * k, 2.0, 71 + k, 81 + k)
+        Lt = torch.from_numpy(L).to(cuda_dev)
+        o = outputs(code, len(L), cuda_dev)
+        reqs.append((code.handle, Lt, len(L), o[0], o[1], None))
+        outs.append(o)
+        refs.append(ldpc.decode(code, p, Lt))
+    ldpc.ldpc_decode_multi(reqs, p)
+    torch.cuda.synchronize()
+    for o, (rb, ri, _) in zip(outs, refs):
+        assert torch.equal(o[0], rb) and torch.equal(o[1], ri)
