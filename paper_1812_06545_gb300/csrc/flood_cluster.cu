@@ -375,14 +375,23 @@ static cudaError_t launch_cluster(const ClusterArgs &a, size_t smem, int64_t n_c
     cfg.blockDim = dim3(cl_threads<DMAX>(), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    int clusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&clusters, k_flood_cluster<DMAX, MsgT>, &cfg);
-    if (e != cudaSuccess || clusters < 1) {
-        cudaGetLastError();
-        int dev = 0, nsm = 2;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        clusters = nsm / CLUSTER_CTAS;
+    // clusters that fit the device at once, queried once per device and shared-memory size
+    static int cached[64];
+    static size_t cached_smem[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    int clusters = __atomic_load_n(&cached[dev], __ATOMIC_RELAXED);
+    if (clusters < 1 || __atomic_load_n(&cached_smem[dev], __ATOMIC_RELAXED) != smem) {
+        e = cudaOccupancyMaxActiveClusters(&clusters, k_flood_cluster<DMAX, MsgT>, &cfg);
+        if (e != cudaSuccess || clusters < 1) {
+            cudaGetLastError();
+            int nsm = 2;
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            clusters = nsm / CLUSTER_CTAS;
+        }
+        __atomic_store_n(&cached_smem[dev], smem, __ATOMIC_RELAXED);
+        __atomic_store_n(&cached[dev], clusters, __ATOMIC_RELAXED);
     }
     if ((int64_t)clusters > n_cw) clusters = (int)n_cw;
     LaunchScope ls(F_SLOTS, s);
