@@ -78,6 +78,7 @@ def streaming_roofline(ldpc, iters_np, steps, N, E, T, hbm_peak, peak_src):
     traffic = stored_traffic("k_flood_cn", CN_SOURCES)
     return {"bound": "hbm", "kernel": "k_flood_cn (check-node phase)", "achieved": cn_gbs, "peak": hbm_peak,
             "unit": "GB/s", "frac": (cn_gbs / hbm_peak) if cn_gbs else None, "peak_source": peak_src,
+            "frac_of_nominal_7900": (cn_gbs / 7900.0) if cn_gbs else None,
             "traffic": traffic, "launches": n_cn, "avg_launch_ms": cn_ms / max(n_cn, 1),
             "algorithmic_bytes_per_cw_iteration": 4 * N + 8 * E,
             "variable_node": {"achieved": vn_gbs, "frac": (vn_gbs / hbm_peak) if vn_gbs else None,
@@ -687,6 +688,8 @@ def main():
             "latency_ms": {"what": "one 8192-codeword decode call", "p50": float(np.percentile(lat, 50)),
                            "p99": float(np.percentile(lat, 99))},
             "avg_iterations": float(np.mean(np.concatenate(iters_np))), "fer": fer,
+            "coded_bit_iterations_per_s": world * args.steps * N * float(sum(int(it.sum()) for it in iters_np)) /
+                                          (ms_max * 1e-3),
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
 
     gpu_bits = {"flood_f32": [b.cpu().numpy() for b in bits]}
