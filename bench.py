@@ -86,6 +86,26 @@ def streaming_roofline(ldpc, iters_np, steps, N, E, T, hbm_peak, peak_src):
                               "algorithmic_bytes_per_cw_iteration": 4 * E + 8 * N}}
 
 
+# ------------------------------------------------------------------ replicas (N > 1)
+
+def reduce_max(dist, x: float, device=None) -> float:
+    """The maximum of x over all ranks (x itself without a process group): the job's time is
+    the slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbps(world: int, codewords_per_rank: int, K: int, seconds_max: float) -> float:
+    """Information Gbit/s of the whole job: the codewords every rank decoded (weak scaling, the
+    same work per rank) over the slowest rank's time."""
+    return world * codewords_per_rank * K / seconds_max / 1e9
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -557,11 +577,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(dist, x, dev)
 
     # ---------------- inputs resident in HBM before timing
     w, B, Z, frames = workload_frames(WORKLOAD, rank)
@@ -625,7 +641,7 @@ def main():
     clocks = sampler.stop() if sampler else None
     ms_max = max_over_ranks(ms)
     units = world * args.steps * len(xs) * n_per_batch
-    value = units * code.K / (ms_max * 1e-3) / 1e9
+    value = whole_job_gbps(world, args.steps * len(xs) * n_per_batch, code.K, ms_max * 1e-3)
 
     # FER and iteration statistics of the last timed step
     fer = {}
