@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
     int32_t *sreq = bad + SLOTS_MAX;                             // [SLOTS_MAX] request of the next codeword
     int64_t *fresh = reinterpret_cast<int64_t *>(sreq + SLOTS_MAX);  // [SLOTS_MAX] next codeword (request-local)
     int32_t *misc = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);  // [4] group hand-over
-    int32_t *t_ent = misc + 4;
+    int4 *t_ed = reinterpret_cast<int4 *>(misc + 4);  // 16-byte aligned: the head is a multiple of 16 bytes
     float *APPs = reinterpret_cast<float *>(smem + slots_smem_head(a.tbl_ints));
 
     const int tid = threadIdx.x, nth = blockDim.x;
@@ -80,18 +80,21 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
         const int C = gd.C, G = gd.C / V;
         const int strideA = slot_stride(N, Z), strideR = slot_stride(gd.E, Z);
         MsgT *Rs = reinterpret_cast<MsgT *>(APPs + (((size_t)C * strideA + 3) & ~(size_t)3));
-        int32_t *t_colent = t_ent + nnz;
+        int32_t *t_colent = reinterpret_cast<int32_t *>(t_ed + nnz);
         int32_t *t_rowptr = t_colent + nnz;
         int32_t *t_colptr = t_rowptr + mb + 1;
-        // tables, pre-scaled: t_ent[b] = (s << 16) | (j * Z) for block b; t_colent[i] = b * Z
-        // for the i-th block of the column lists.  Messages are stored at the variable's
-        // position inside its block: edge (b, r) of check row r lives at b*Z + (r + s) mod Z,
-        // so the check-node phase computes the wrap once for both addresses and the
-        // variable-node phase, summing column position r of block column j, reads b*Z + r.
+        // tables, pre-scaled to byte offsets from a thread's own bases (position r of slot
+        // group g): t_ed[b] is the edge descriptor of block b (see EdgeRef); t_colent[i] is
+        // the message offset of block row-major index b*Z for the i-th block of the column
+        // lists.  Messages are stored at the variable's position inside its block: edge
+        // (b, r) of check row r lives at b*Z + (r + s) mod Z, so the check-node phase
+        // computes the wrap once for both addresses and the variable-node phase, summing
+        // column position r of block column j, reads b*Z + r.
+        constexpr int SA = (int)sizeof(float) * V, SR = (int)sizeof(MsgT) * V;
         for (int i = tid; i < nnz; i += nth) {
-            const int e = cd->ent[i];
-            t_ent[i] = ((e & 0xffff) << 16) | ((e >> 16) * Z);
-            t_colent[i] = (cd->colent[i] >> 16) * Z;
+            const int e = cd->ent[i], j = e >> 16, sh = e & 0xffff;
+            t_ed[i] = make_int4(SA * (j * Z + sh), SR * (i * Z + sh), Z - sh, 0);
+            t_colent[i] = SR * (cd->colent[i] >> 16) * Z;
         }
         for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
         for (int i = tid; i <= nb; i += nth) t_colptr[i] = cd->colptr[i];
@@ -122,6 +125,9 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
 
         float *A = APPs + (size_t)(mine ? g : 0) * strideA * V;
         MsgT *Rc = Rs + (size_t)(mine ? g : 0) * strideR * V;
+        const char *Ar = reinterpret_cast<const char *>(A + r * V);
+        char *Rr = reinterpret_cast<char *>(Rc + r * V);
+        const int ZA = SA * Z, ZR = SR * Z;
         int64_t cw[V];  // request-local codeword in each of this thread's slots (-1: empty)
         int rq[V];      // its request
         int t[V];       // iterations completed on it
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                 for (int v = 0; v < V; v++) pbad[v] = 0;
                 for (int l = 0; l < mb; l++) {
                     const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
-                    slot_check_dispatch<2, DMAX, V, MsgT>(dc, t_ent + b0, b0 * Z, A, Rc, r, Z, X, Xb, pbad);
+                    slot_check_dispatch<2, DMAX, V, MsgT>(dc, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
                 }
 #pragma unroll
                 for (int v = 0; v < V; v++)
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                             const int i1 = t_colptr[j + 1];
                             for (int i = t_colptr[j]; i < i1; i++) {
                                 float rv[V];
-                                SMsg<MsgT, V>::ld(Rc + (t_colent[i] + r) * V, rv);
+                                SMsg<MsgT, V>::ld(at<MsgT>(Rr, t_colent[i]), rv);
 #pragma unroll
                                 for (int v = 0; v < V; v++) sacc[v] += rv[v];
                             }
@@ -308,7 +314,7 @@ static size_t max_smem_optin()
     return v > 0 ? (size_t)v : 227 * 1024;
 }
 
-static int tables_ints(const CodeDev &h) { return 2 * h.nnz + h.mb + 1 + h.nb + 1; }
+static int tables_ints(const CodeDev &h) { return 5 * h.nnz + h.mb + 1 + h.nb + 1; }
 
 // Shared memory of C slots of a code: the APP region (16-byte aligned end) and the messages.
 static size_t slots_bytes(const CodeDev &h, int msg, int C)

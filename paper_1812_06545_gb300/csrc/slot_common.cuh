@@ -91,9 +91,28 @@ __host__ __device__ constexpr int next_degree(int d) { return d < 8 ? d + 1 : d 
 
 // One check of row r for V slots: Q = APP - R over its edges, phi rule, messages written
 // in place (at the variable's position), parity of the APP sign bits accumulated in pbad.
+// Edge descriptors of one check row (built once per code when a CTA loads its tables): for
+// edge k of block b = (row l, column j, shift s), .x = byte offset of the posterior
+// (j*Z + s) and .y of the message (b*Z + s), both scaled by the element size and V, and
+// .z = Z - s.  Row r of the block row reaches variable position (r + s) mod Z, so the
+// thread's offsets are .x and .y from its own bases (position r), less one block (ZA, ZR
+// bytes) when r >= .z.
+struct EdgeRef {
+    int oa, orr;
+};
+__device__ __forceinline__ EdgeRef edge_ref(const int4 d, int r, int ZA, int ZR)
+{
+    const bool w = r >= d.z;
+    return {d.x - (w ? ZA : 0), d.y - (w ? ZR : 0)};
+}
+template <typename T>
+__device__ __forceinline__ const T *at(const char *base, int off) { return reinterpret_cast<const T *>(base + off); }
+template <typename T>
+__device__ __forceinline__ T *at(char *base, int off) { return reinterpret_cast<T *>(base + off); }
+
 template <int D, bool EXACT, int V, typename MsgT>
-__device__ __forceinline__ void slot_check(int dc, const int32_t *__restrict__ ent, int bZ, const float *A, MsgT *Rc,
-                                           int r, int Z, float X, float Xb, uint32_t (&pbad)[V])
+__device__ __forceinline__ void slot_check(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr, int r,
+                                           int ZA, int ZR, float X, float Xb, uint32_t (&pbad)[V])
 {
     constexpr uint32_t kSign = 0x80000000u;
     float av[D][V];
@@ -104,13 +123,11 @@ __device__ __forceinline__ void slot_check(int dc, const int32_t *__restrict__ e
 #pragma unroll
     for (int k = 0; k < D; k++) {
         if (EXACT || k < dc) {
-            const int e = ent[k];
-            int x = r + (e >> 16);
-            x -= (x >= Z) ? Z : 0;
-            xo[k] = x;
+            const EdgeRef e = edge_ref(ed[k], r, ZA, ZR);
+            xo[k] = e.orr;
             float ap[V], rv[V];
-            SMsg<float, V>::ld(A + ((e & 0xffff) + x) * V, ap);
-            SMsg<MsgT, V>::ld(Rc + (bZ + k * Z + x) * V, rv);
+            SMsg<float, V>::ld(at<float>(Ar, e.oa), ap);
+            SMsg<MsgT, V>::ld(at<MsgT>(Rr, e.orr), rv);
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 const float q = ap[v] - rv[v];
@@ -144,7 +161,7 @@ __device__ __forceinline__ void slot_check(int dc, const int32_t *__restrict__ e
                     pre[v] += fabsf(av[k][v]);
                     out[v] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
                 }
-                SMsg<MsgT, V>::st(Rc + (bZ + k * Z + xo[k]) * V, out);
+                SMsg<MsgT, V>::st(at<MsgT>(Rr, xo[k]), out);
             }
         }
     } else {
@@ -182,7 +199,7 @@ __device__ __forceinline__ void slot_check(int dc, const int32_t *__restrict__ e
                     const float mag = fminf(s_phi_out(ak == amax[v] ? sx[v] : S[v] - ak), X);
                     out[v] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
                 }
-                SMsg<MsgT, V>::st(Rc + (bZ + k * Z + xo[k]) * V, out);
+                SMsg<MsgT, V>::st(at<MsgT>(Rr, xo[k]), out);
             }
         }
     }
@@ -221,8 +238,8 @@ __device__ __forceinline__ float2 phi_out2(float2 s2)
 }
 
 template <int D, bool EXACT, typename MsgT>
-__device__ __forceinline__ void slot_check_pair(int dc, const int32_t *__restrict__ ent, int bZ, const float *A,
-                                                MsgT *Rc, int r, int Z, float X, float Xb, uint32_t (&pbad)[2])
+__device__ __forceinline__ void slot_check_pair(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr, int r,
+                                                int ZA, int ZR, float X, float Xb, uint32_t (&pbad)[2])
 {
     constexpr uint32_t kSign = 0x80000000u;
     float2 av[D];
@@ -231,13 +248,11 @@ __device__ __forceinline__ void slot_check_pair(int dc, const int32_t *__restric
 #pragma unroll
     for (int k = 0; k < D; k++) {
         if (EXACT || k < dc) {
-            const int e = ent[k];
-            int x = r + (e >> 16);
-            x -= (x >= Z) ? Z : 0;
-            xo[k] = x;
+            const EdgeRef e = edge_ref(ed[k], r, ZA, ZR);
+            xo[k] = e.orr;
             float ap[2], rv[2];
-            SMsg<float, 2>::ld(A + ((e & 0xffff) + x) * 2, ap);
-            SMsg<MsgT, 2>::ld(Rc + (bZ + k * Z + x) * 2, rv);
+            SMsg<float, 2>::ld(at<float>(Ar, e.oa), ap);
+            SMsg<MsgT, 2>::ld(at<MsgT>(Rr, e.orr), rv);
             const float2 q = __ffma2_rn(f2(rv[0], rv[1]), f2(-1.0f, -1.0f), f2(ap[0], ap[1]));
             par0 ^= __float_as_uint(ap[0]);
             par1 ^= __float_as_uint(ap[1]);
@@ -265,7 +280,7 @@ __device__ __forceinline__ void slot_check_pair(int dc, const int32_t *__restric
                 float out[2];
                 out[0] = __uint_as_float(__float_as_uint(fminf(mag.x, X)) | ((__float_as_uint(av[k].x) ^ sg0) & kSign));
                 out[1] = __uint_as_float(__float_as_uint(fminf(mag.y, X)) | ((__float_as_uint(av[k].y) ^ sg1) & kSign));
-                SMsg<MsgT, 2>::st(Rc + (bZ + k * Z + xo[k]) * 2, out);
+                SMsg<MsgT, 2>::st(at<MsgT>(Rr, xo[k]), out);
             }
         }
     } else {
@@ -295,7 +310,7 @@ __device__ __forceinline__ void slot_check_pair(int dc, const int32_t *__restric
                 float out[2];
                 out[0] = __uint_as_float(__float_as_uint(fminf(mag.x, X)) | ((__float_as_uint(av[k].x) ^ sg0) & kSign));
                 out[1] = __uint_as_float(__float_as_uint(fminf(mag.y, X)) | ((__float_as_uint(av[k].y) ^ sg1) & kSign));
-                SMsg<MsgT, 2>::st(Rc + (bZ + k * Z + xo[k]) * 2, out);
+                SMsg<MsgT, 2>::st(at<MsgT>(Rr, xo[k]), out);
             }
         }
     }
@@ -307,31 +322,31 @@ __device__ __forceinline__ void slot_check_pair(int dc, const int32_t *__restric
 #define LDPC_SLOTS_PAIRED_FP 1  // packed FP32x2 arithmetic for two codewords per thread
 #endif
 template <int D, bool EXACT, int V, typename MsgT>
-__device__ __forceinline__ void slot_check_v(int dc, const int32_t *__restrict__ ent, int bZ, const float *A, MsgT *Rc,
-                                             int r, int Z, float X, float Xb, uint32_t (&pbad)[V])
+__device__ __forceinline__ void slot_check_v(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr, int r,
+                                             int ZA, int ZR, float X, float Xb, uint32_t (&pbad)[V])
 {
     if constexpr (V == 2 && LDPC_SLOTS_PAIRED_FP)
-        slot_check_pair<D, EXACT, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+        slot_check_pair<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
     else
-        slot_check<D, EXACT, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+        slot_check<D, EXACT, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
 }
 
 template <int D, int DMAX, int V, typename MsgT>
-__device__ __forceinline__ void slot_check_dispatch(int dc, const int32_t *__restrict__ ent, int bZ, const float *A,
-                                                    MsgT *Rc, int r, int Z, float X, float Xb, uint32_t (&pbad)[V])
+__device__ __forceinline__ void slot_check_dispatch(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr,
+                                                    int r, int ZA, int ZR, float X, float Xb, uint32_t (&pbad)[V])
 {
     if constexpr (D >= DMAX) {
-        slot_check_v<DMAX, false, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+        slot_check_v<DMAX, false, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
     } else if constexpr (D <= 8) {
         if (dc == D)
-            slot_check_v<D, true, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+            slot_check_v<D, true, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
         else
-            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
     } else {
         if (dc <= D)
-            slot_check_v<D, false, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+            slot_check_v<D, false, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
         else
-            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb, pbad);
+            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
     }
 }
 
