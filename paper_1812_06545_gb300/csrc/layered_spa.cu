@@ -66,27 +66,34 @@ struct MsgIO<__half> {
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
 };
 
-// One check of row r in the layer whose blocks start at table entry `ent` (R of block k of
-// the layer at bZ + k*Z + r), computed from and written back to the slot's APP and R.
+// Edge descriptor of block b = (row l, column j, shift s) for the layered slots: .x = byte
+// offset of the posterior j*Z + s, .y = byte offset of the message row b*Z, .z = Z - s.
+// Check row r reaches variable position (r + s) mod Z: .x from the thread's posterior base
+// (position r), less one block (ZA bytes) when r >= .z; its message is .y from its message
+// base (row r), with no wrap.
+__device__ __forceinline__ int lspa_app_off(const int4 d, int r, int ZA) { return d.x - (r >= d.z ? ZA : 0); }
+
+// One check of row r in the layer whose blocks start at descriptor `ed`, computed from and
+// written back to the slot's APP (thread base Ar) and R (thread base Rr).
 template <int D, bool EXACT, typename MsgT>
-__device__ __forceinline__ void layer_check(int dc, const int32_t *__restrict__ ent, int bZ, float *A, MsgT *Rc, int r,
-                                            int Z, float X, float Xb)
+__device__ __forceinline__ void layer_check(int dc, const int4 *__restrict__ ed, char *Ar, char *Rr, int r, int ZA,
+                                            float X, float Xb)
 {
     constexpr uint32_t kSign = 0x80000000u;
-    MsgT *Rr = Rc + bZ + r;
+    // the layer's messages: row r of its blocks, one block (Z messages) apart
+    MsgT *Rl = at<MsgT>(Rr, ed[0].y);
+    const int Zm = ZA / (int)sizeof(float);
     float a[D];                     // phi(clampX |Q|) in base-2 units, carrying the sign bit of Q
-    int ao[D <= 8 ? D : 1];         // APP index of the edge's variable
+    int ao[D <= 8 ? D : 1];         // byte offset of the edge's variable in APP
     uint32_t sg = 0;
     if constexpr (D <= 8 && sizeof(MsgT) == 4) {
         float q[D];
 #pragma unroll
         for (int k = 0; k < D; k++) {
             if (EXACT || k < dc) {
-                const int e = ent[k];
-                int x = r + (e >> 16);
-                x -= (x >= Z) ? Z : 0;
-                ao[k] = (e & 0xffff) + x;
-                q[k] = A[ao[k]] - MsgIO<MsgT>::ld(Rr + k * Z);
+                const int4 d = ed[k];
+                ao[k] = lspa_app_off(d, r, ZA);
+                q[k] = *at<float>(Ar, ao[k]) - MsgIO<MsgT>::ld(Rl + k * Zm);
                 const uint32_t qs = __float_as_uint(q[k]) & kSign;
                 sg ^= qs;
                 a[k] = __uint_as_float(__float_as_uint(fminf(s_psi_in(fminf(fabsf(q[k]), X)), Xb)) | qs);
@@ -104,7 +111,7 @@ __device__ __forceinline__ void layer_check(int dc, const int32_t *__restrict__ 
                 const float mag = fminf(s_phi_out(pre + sf[k + 1]), X);
                 pre += fabsf(a[k]);
                 const float out = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(a[k]) ^ sg) & kSign));
-                A[ao[k]] = q[k] + MsgIO<MsgT>::st(Rr + k * Z, out);
+                *at<float>(Ar, ao[k]) = q[k] + MsgIO<MsgT>::st(Rl + k * Zm, out);
             }
         }
     } else {
@@ -117,11 +124,10 @@ __device__ __forceinline__ void layer_check(int dc, const int32_t *__restrict__ 
 #pragma unroll
         for (int k = 0; k < D; k++) {
             if (EXACT || k < dc) {
-                const int e = ent[k];
-                int x = r + (e >> 16);
-                x -= (x >= Z) ? Z : 0;
-                if constexpr (kHoldIdx) ao[k] = (e & 0xffff) + x;
-                const float q = A[(e & 0xffff) + x] - MsgIO<MsgT>::ld(Rr + k * Z);
+                const int4 d = ed[k];
+                const int oa = lspa_app_off(d, r, ZA);
+                if constexpr (kHoldIdx) ao[k] = oa;
+                const float q = *at<float>(Ar, oa) - MsgIO<MsgT>::ld(Rl + k * Zm);
                 const uint32_t qs = __float_as_uint(q) & kSign;
                 sg ^= qs;
                 const float m = fminf(s_psi_in(fminf(fabsf(q), X)), Xb);
@@ -142,39 +148,39 @@ __device__ __forceinline__ void layer_check(int dc, const int32_t *__restrict__ 
                 const float mag = fminf(s_phi_out(ak == amax ? sx : S - ak), X);
                 const float out = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(a[k]) ^ sg) & kSign));
                 int ai;
-                if constexpr (kHoldIdx) {
+                if constexpr (kHoldIdx)
                     ai = ao[k];
-                } else {
-                    const int e = ent[k];
-                    int x = r + (e >> 16);
-                    x -= (x >= Z) ? Z : 0;
-                    ai = (e & 0xffff) + x;
-                }
-                const float q = A[ai] - MsgIO<MsgT>::ld(Rr + k * Z);
-                A[ai] = q + MsgIO<MsgT>::st(Rr + k * Z, out);
+                else
+                    ai = lspa_app_off(ed[k], r, ZA);
+                const float q = *at<float>(Ar, ai) - MsgIO<MsgT>::ld(Rl + k * Zm);
+                *at<float>(Ar, ai) = q + MsgIO<MsgT>::st(Rl + k * Zm, out);
             }
         }
     }
 }
 
 template <int D, int DMAX, typename MsgT>
-__device__ __forceinline__ void layer_check_dispatch(int dc, const int32_t *__restrict__ ent, int bZ, float *A,
-                                                     MsgT *Rc, int r, int Z, float X, float Xb)
+__device__ __forceinline__ void layer_check_dispatch(int dc, const int4 *__restrict__ ed, char *Ar, char *Rr, int r,
+                                                     int ZA, float X, float Xb)
 {
     if constexpr (D >= DMAX) {
-        layer_check<DMAX, false, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb);
+        layer_check<DMAX, false, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb);
     } else if constexpr (D <= 8) {
         if (dc == D)
-            layer_check<D, true, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb);
+            layer_check<D, true, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb);
         else
-            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb);
+            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb);
     } else {
         if (dc <= D)
-            layer_check<D, false, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb);
+            layer_check<D, false, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb);
         else
-            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, bZ, A, Rc, r, Z, X, Xb);
+            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb);
     }
 }
+
+// Table space (ints) ahead of the slots: four per block for its edge descriptor, then the
+// block-row pointers.
+__host__ __device__ inline int lspa_tables_ints(int nnz, int mb) { return 4 * nnz + mb + 1; }
 
 // Threads per CTA for an instance: high-degree checks keep more values live per thread.
 // fp32 slots are limited to a few per CTA by shared memory, so their threads get more
@@ -206,17 +212,18 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
     int32_t *bad = reinterpret_cast<int32_t *>(smem);                 // [SLOTS_MAX] unsatisfied check seen
     int32_t *gany = bad + SLOTS_MAX;                                   // [SLOTS_MAX / 2][2] group vote
     int64_t *fresh = reinterpret_cast<int64_t *>(gany + SLOTS_MAX);    // [SLOTS_MAX] the slot's codeword
-    int32_t *t_ent = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);   // (s << 16) | j*Z per block
-    int32_t *t_rowptr = t_ent + nnz;
-    float *APPs = reinterpret_cast<float *>(smem + slots_smem_head(nnz + mb + 1));
+    int4 *t_ed = reinterpret_cast<int4 *>(fresh + SLOTS_MAX);         // edge descriptor per block
+    int32_t *t_rowptr = reinterpret_cast<int32_t *>(t_ed + nnz);
+    float *APPs = reinterpret_cast<float *>(smem + slots_smem_head(lspa_tables_ints(nnz, mb)));
     MsgT *Rs = reinterpret_cast<MsgT *>(APPs + (size_t)C * a.strideA);
 
     const int tid = threadIdx.x, nth = blockDim.x;
     const float X = a.X, Xb = a.X * kSLog2e;
     for (int i = tid; i < nnz; i += nth) {
-        const int e = cd->ent[i];
-        t_ent[i] = ((e & 0xffff) << 16) | ((e >> 16) * Z);
+        const int e = cd->ent[i], sh = e & 0xffff;
+        t_ed[i] = make_int4((int)sizeof(float) * ((e >> 16) * Z + sh), (int)sizeof(MsgT) * i * Z, Z - sh, 0);
     }
+    const int ZA = (int)sizeof(float) * Z;
     for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
     const int g = tid / TPG, u = tid - (tid / TPG) * TPG;
     const int c = g * K + u / Z, r = u - (u / Z) * Z;
@@ -232,6 +239,7 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
     if (g * K >= C) return;  // whole warps beyond the last group
     float *A = APPs + (size_t)(mine ? c : 0) * a.strideA;
     MsgT *Rc = Rs + (size_t)(mine ? c : 0) * a.strideR;
+    char *Ar = reinterpret_cast<char *>(A + r), *Rr = reinterpret_cast<char *>(Rc + r);
     int ph = 0;
     // OR of a predicate over the group (every thread of the group calls it at the same
     // point; the vote alternates between two words so that clearing the next one races with
@@ -266,7 +274,7 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
         for (int l = 0; l < mb; l++) {
             if (busy) {
                 const int b0 = t_rowptr[l];
-                layer_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ent + b0, b0 * Z, A, Rc, r, Z, X, Xb);
+                layer_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0, Ar, Rr, r, ZA, X, Xb);
             }
             group_sync(g, TPG);
         }
@@ -276,12 +284,8 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
             uint32_t par_any = 0;
             for (int l = 0; l < mb; l++) {
                 uint32_t par = 0;
-                for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++) {
-                    const int e = t_ent[b];
-                    int x = r + (e >> 16);
-                    x -= (x >= Z) ? Z : 0;
-                    par ^= __float_as_uint(A[(e & 0xffff) + x]);
-                }
+                for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++)
+                    par ^= __float_as_uint(*at<float>(Ar, lspa_app_off(t_ed[b], r, ZA)));
                 par_any |= par;
             }
             if (par_any & 0x80000000u) bad[c] = 1;
@@ -335,7 +339,7 @@ static int lspa_threads_for(int dc_max, int msg)
 
 static size_t lspa_smem(const CodeDev &h, int msg, int C)
 {
-    return slots_smem_head(h.nnz + h.mb + 1) + (size_t)C * lspa_slot_bytes(h, msg);
+    return slots_smem_head(lspa_tables_ints(h.nnz, h.mb)) + (size_t)C * lspa_slot_bytes(h, msg);
 }
 
 // Slots per CTA and their grouping: the most slots that fit the instance's threads, 15 named
