@@ -53,6 +53,38 @@ struct FloodMultiArgs {
     float X;
 };
 
+// Sum of the messages of one variable (column degree dv, message offsets ce) into sacc, in
+// the order of the column lists.  The common degrees get straight-line bodies; every lane
+// of a warp takes the same branch (a warp covers one block column).
+template <int D, int V, typename MsgT>
+__device__ __forceinline__ void vn_sum(const int32_t *__restrict__ ce, const char *Rr, float (&sacc)[V])
+{
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        float rv[V];
+        SMsg<MsgT, V>::ld(at<MsgT>(Rr, ce[k]), rv);
+#pragma unroll
+        for (int v = 0; v < V; v++) sacc[v] += rv[v];
+    }
+}
+template <int V, typename MsgT>
+__device__ __forceinline__ void vn_column(int dv, const int32_t *__restrict__ ce, const char *Rr, float (&sacc)[V])
+{
+    if (dv == 3)
+        vn_sum<3, V, MsgT>(ce, Rr, sacc);
+    else if (dv == 2)
+        vn_sum<2, V, MsgT>(ce, Rr, sacc);
+    else if (dv == 4)
+        vn_sum<4, V, MsgT>(ce, Rr, sacc);
+    else
+        for (int i = 0; i < dv; i++) {
+            float rv[V];
+            SMsg<MsgT, V>::ld(at<MsgT>(Rr, ce[i]), rv);
+#pragma unroll
+            for (int v = 0; v < V; v++) sacc[v] += rv[v];
+        }
+}
+
 template <int DMAX, int V, typename MsgT>
 __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const __grid_constant__ FloodMultiArgs a)
 {
@@ -213,13 +245,8 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                             float sacc[V];
 #pragma unroll
                             for (int v = 0; v < V; v++) sacc[v] = lv[u][v];
-                            const int i1 = t_colptr[j + 1];
-                            for (int i = t_colptr[j]; i < i1; i++) {
-                                float rv[V];
-                                SMsg<MsgT, V>::ld(at<MsgT>(Rr, t_colent[i]), rv);
-#pragma unroll
-                                for (int v = 0; v < V; v++) sacc[v] += rv[v];
-                            }
+                            const int i0 = t_colptr[j];
+                            vn_column<V, MsgT>(t_colptr[j + 1] - i0, t_colent + i0, Rr, sacc);
 #pragma unroll
                             for (int v = 0; v < V; v++)
                                 if (act[v]) A[(j * Z + r) * V + v] = sacc[v] + 0.0f;  // -0 -> +0: sign bit = decision

@@ -210,6 +210,10 @@ __device__ __forceinline__ void lgroup_sync(int grp, int tpg)
         asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(tpg) : "memory");
 }
 
+// Table space (ints) ahead of the slots: two per block for its edge descriptor, then the
+// block-row pointers.
+__host__ __device__ inline int lslots_tables_ints(int nnz, int mb) { return 2 * nnz + mb + 1; }
+
 template <int DMAX>
 __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__restrict__ cd, LayeredSlotArgs a)
 {
@@ -219,15 +223,17 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
     int32_t *bad = reinterpret_cast<int32_t *>(smem);                 // [SLOTS_MAX] unsatisfied check seen
     int32_t *gany = bad + SLOTS_MAX;                                   // [SLOTS_MAX / 2][2] group vote
     int64_t *fresh = reinterpret_cast<int64_t *>(gany + SLOTS_MAX);    // [SLOTS_MAX]
-    int32_t *t_ent = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);   // (s << 16) | j*Z
-    int32_t *t_rowptr = t_ent + nnz;
-    int8_t *APPs = reinterpret_cast<int8_t *>(smem + slots_smem_head(nnz + mb + 1));
+    // edge descriptor of block b = (row l, column j, shift s): .x = j*Z + s, .y = Z - s; check
+    // row r reaches APP offset r + .x, less Z when r >= .y (position (r + s) mod Z of column j)
+    int2 *t_ed = reinterpret_cast<int2 *>(fresh + SLOTS_MAX);
+    int32_t *t_rowptr = reinterpret_cast<int32_t *>(t_ed + nnz);
+    int8_t *APPs = reinterpret_cast<int8_t *>(smem + slots_smem_head(lslots_tables_ints(nnz, mb)));
     int8_t *Rs = APPs + (size_t)C * a.strideA;
 
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < nnz; i += nth) {
-        const int e = cd->ent[i];
-        t_ent[i] = ((e & 0xffff) << 16) | ((e >> 16) * Z);
+        const int e = cd->ent[i], sh = e & 0xffff;
+        t_ed[i] = make_int2((e >> 16) * Z + sh, Z - sh);
     }
     for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
     const int g = tid / TPG, u = tid - (tid / TPG) * TPG;
@@ -287,16 +293,15 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
             if (busy) {
                 const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
                 int8_t *Rr = Rc + b0 * Z + r;
-                int qx[DMAX];  // (wrapped position << 8) | (Q & 0xff): one register per edge
+                int qx[DMAX];  // (APP offset << 8) | (Q & 0xff): one register per edge (N < 2^16)
                 int min1 = 0x7fffffff, min2 = 0x7fffffff, arg = -1;
                 unsigned S = 0;
 #pragma unroll
                 for (int k = 0; k < DMAX; k++) {
                     if (k < dc) {
-                        const int ent = t_ent[b0 + k];
-                        int x = r + (ent >> 16);
-                        x -= (x >= Z) ? Z : 0;
-                        const int qq = sat_i((int)A[(ent & 0xffff) + x] - (int)Rr[k * Z], a.msg_sat);
+                        const int2 d = t_ed[b0 + k];
+                        const int ao = r + d.x - (r >= d.y ? Z : 0);
+                        const int qq = sat_i((int)A[ao] - (int)Rr[k * Z], a.msg_sat);
                         const int mag = qq < 0 ? -qq : qq;
                         if (mag < min1) {
                             min2 = min1;
@@ -306,7 +311,7 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
                             min2 = mag;
                         }
                         S ^= qq < 0 ? 1u : 0u;
-                        qx[k] = (x << 8) | (qq & 0xff);
+                        qx[k] = (ao << 8) | (qq & 0xff);
                     }
                 }
                 const int m1 = (a.alpha_num * min1) >> a.alpha_shift;
@@ -315,11 +320,10 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
                 for (int k = 0; k < DMAX; k++) {
                     if (k < dc) {
                         const int qq = (int)(int8_t)(qx[k] & 0xff);
-                        const int x = qx[k] >> 8;
                         const int magp = (k == arg) ? m2 : m1;
                         const int rn = (S ^ (qq < 0 ? 1u : 0u)) ? -magp : magp;
                         Rr[k * Z] = (int8_t)rn;
-                        A[(t_ent[b0 + k] & 0xffff) + x] = (int8_t)sat_i(qq + rn, a.app_sat);
+                        A[qx[k] >> 8] = (int8_t)sat_i(qq + rn, a.app_sat);
                     }
                 }
             }
@@ -332,10 +336,8 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
             for (int l = 0; l < mb; l++) {
                 unsigned par = 0;
                 for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++) {
-                    const int ent = t_ent[b];
-                    int x = r + (ent >> 16);
-                    x -= (x >= Z) ? Z : 0;
-                    par ^= A[(ent & 0xffff) + x] < 0 ? 1u : 0u;
+                    const int2 d = t_ed[b];
+                    par ^= A[r + d.x - (r >= d.y ? Z : 0)] < 0 ? 1u : 0u;
                 }
                 par_any |= par;
             }
@@ -400,7 +402,7 @@ static cudaError_t launch_layered(const CodeDev &h, const CodeDev *d, const Laye
 
 static size_t lslots_smem(const CodeDev &h, int C)
 {
-    return slots_smem_head(h.nnz + h.mb + 1) + (size_t)C * (((h.N + 15) & ~15) + ((h.E + 15) & ~15));
+    return slots_smem_head(lslots_tables_ints(h.nnz, h.mb)) + (size_t)C * (((h.N + 15) & ~15) + ((h.E + 15) & ~15));
 }
 
 // Slots per CTA and their grouping: the most slots that fit 1024 threads, 15 named barriers
