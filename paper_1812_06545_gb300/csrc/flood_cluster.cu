@@ -55,7 +55,7 @@ __host__ __device__ inline int cl_owner(const int *split, int x)
 // One check of an owned row: Q = APP - R over its edges (posteriors wherever they live), the
 // phi rule, messages written in place; returns the parity of the posteriors' sign bits.
 template <int D, bool EXACT, typename MsgT>
-__device__ __forceinline__ uint32_t cl_check(int dc, const int32_t *__restrict__ ent, MsgT *Rr, const float *app_0,
+__device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed, MsgT *Rr, const float *app_0,
                                              const float *app_1, int r, int Z, float X, float Xb)
 {
     constexpr uint32_t kSign = 0x80000000u;
@@ -64,10 +64,8 @@ __device__ __forceinline__ uint32_t cl_check(int dc, const int32_t *__restrict__
 #pragma unroll
     for (int k = 0; k < D; k++) {
         if (EXACT || k < dc) {
-            const int e = ent[k];
-            int x = r + (e >> 20);
-            x -= (x >= Z) ? Z : 0;
-            const float ap = ((e >> 19) & 1 ? app_1 : app_0)[(e & 0x7ffff) + x];
+            const int4 d = ed[k];
+            const float ap = (d.z ? app_1 : app_0)[d.x + r - (r >= d.y ? Z : 0)];
             const float qv = ap - (float)Rr[k * Z];
             par ^= __float_as_uint(ap);
             const uint32_t qs = __float_as_uint(qv) & kSign;
@@ -117,7 +115,7 @@ __device__ __forceinline__ uint32_t cl_check(int dc, const int32_t *__restrict__
 }
 
 template <int D, int DMAX, typename MsgT>
-__device__ __forceinline__ uint32_t cl_check_dispatch(int dc, const int32_t *__restrict__ ent, MsgT *Rr,
+__device__ __forceinline__ uint32_t cl_check_dispatch(int dc, const int4 *__restrict__ ent, MsgT *Rr,
                                                       const float *app_0, const float *app_1, int r, int Z, float X,
                                                       float Xb)
 {
@@ -130,6 +128,44 @@ __device__ __forceinline__ uint32_t cl_check_dispatch(int dc, const int32_t *__r
         if (dc <= D) return cl_check<D, false, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
         return cl_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
     }
+}
+
+// Sum of the messages of variable position c of one block column (column degree dv; entry
+// descriptors cd, see the kernel) onto sum, in the order of the column lists: straight-line
+// bodies for the common degrees (every lane of a warp takes the same branch).
+template <int D, typename MsgT>
+__device__ __forceinline__ float cl_vn_sum(const int4 *__restrict__ cd, const MsgT *r_0, const MsgT *r_1, int c, int Z,
+                                           float sum)
+{
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        const int4 d = cd[k];
+        sum += (float)(d.z ? r_1 : r_0)[d.x + c + (c < d.y ? Z : 0)];
+    }
+    return sum;
+}
+template <typename MsgT>
+__device__ __forceinline__ float cl_vn_column(int dv, const int4 *__restrict__ cd, const MsgT *r_0, const MsgT *r_1,
+                                              int c, int Z, float sum)
+{
+    switch (dv) {
+    case 2: return cl_vn_sum<2, MsgT>(cd, r_0, r_1, c, Z, sum);
+    case 3: return cl_vn_sum<3, MsgT>(cd, r_0, r_1, c, Z, sum);
+    case 4: return cl_vn_sum<4, MsgT>(cd, r_0, r_1, c, Z, sum);
+    default:
+        for (int k = 0; k < dv; k++) {
+            const int4 d = cd[k];
+            sum += (float)(d.z ? r_1 : r_0)[d.x + c + (c < d.y ? Z : 0)];
+        }
+        return sum;
+    }
+}
+
+// Shared memory ahead of the posterior array: flags and codeword (16 bytes), the block-row
+// and block-column pointers, then two descriptors (int4) per block.
+__host__ __device__ inline size_t cl_tables_bytes(int nnz)
+{
+    return (((size_t)16 + 4 * (MB_MAX + 1 + NB_MAX + 1) + 15) & ~(size_t)15) + (size_t)32 * nnz;
 }
 
 // threads per CTA: higher check degrees keep more values live per thread
@@ -152,10 +188,15 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
     int32_t *flags = reinterpret_cast<int32_t *>(smem);
     int64_t *cwp = reinterpret_cast<int64_t *>(smem + 8);
     int32_t *t_rowptr = reinterpret_cast<int32_t *>(smem + 16);  // [mb + 1]
-    int32_t *t_ent = t_rowptr + MB_MAX + 1;                       // [nnz] (shift << 20) | owner APP base
-    int32_t *t_colptr = t_ent + NNZ_MAX;                          // [nb + 1]
-    int32_t *t_cent = t_colptr + NB_MAX + 1;                      // [nnz] (shift << 20) | owner R base
-    int32_t *t_cown = t_cent + NNZ_MAX;                           // [nnz] owner of the entry's row
+    int32_t *t_colptr = t_rowptr + MB_MAX + 1;                    // [nb + 1]
+    // check-node descriptor of block b = (row l, column j, shift s): .x = the posterior
+    // index of position s of column j in its owner, .y = Z - s, .z = the owner; check row r
+    // reads .x + r, less Z when r >= .y.  Variable-node descriptor of the i-th entry of the
+    // column lists (block b, shift s): .x = the index of b's message row in its owner, less
+    // s, .y = s, .z = the owner; variable position c reads .x + c, plus Z when c < .y
+    // (message row (c - s) mod Z, which holds the edge of variable c).
+    int4 *t_ed = reinterpret_cast<int4 *>(smem + (((size_t)16 + 4 * (MB_MAX + 1 + NB_MAX + 1) + 15) & ~(size_t)15));
+    int4 *t_cd = t_ed + nnz;
     const int row0 = a.row_split[q], row1 = a.row_split[q + 1];
     // block b's owner of posteriors and its base there; column entry's owner of messages
     for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
@@ -165,7 +206,7 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
     for (int b = tid; b < nnz; b += nth) {
         const int e = cd->ent[b];
         const int j = e >> 16, s = e & 0xffff;
-        t_ent[b] = (s << 20) | (a.col_owner[j] << 19) | (a.col_slot[j] * Z);
+        t_ed[b] = make_int4(a.col_slot[j] * Z + s, Z - s, a.col_owner[j], 0);
     }
     for (int i = tid; i < nnz; i += nth) {
         const int ce = cd->colent[i];
@@ -173,10 +214,9 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
         int l = 0;
         while (l < mb - 1 && b >= cd->rowptr[l + 1]) l++;
         const int qo = cl_owner(a.row_split, l);
-        t_cent[i] = (s << 20) | ((b - cd->rowptr[a.row_split[qo]]) * Z);
-        t_cown[i] = qo;
+        t_cd[i] = make_int4((b - cd->rowptr[a.row_split[qo]]) * Z - s, s, qo, 0);
     }
-    const size_t off_app = (((size_t)(16 + 4 * (2 * NNZ_MAX + MB_MAX + NB_MAX + 2 + NNZ_MAX))) + 15) & ~(size_t)15;
+    const size_t off_app = cl_tables_bytes(nnz);
     float *app = reinterpret_cast<float *>(smem + off_app);
     // R starts at the same offset in every CTA (after the largest posterior share), so that
     // mapping an address into another CTA of the cluster finds that CTA's messages
@@ -224,7 +264,7 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
                 const int lr = w / Z, r = w - lr * Z;
                 const int l = row0 + lr;
                 const int b0 = t_rowptr[l];
-                const uint32_t par = cl_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ent + b0,
+                const uint32_t par = cl_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0,
                                                                       R + (b0 - blk0) * Z + r, app_0, app_1, r, Z,
                                                                       X, Xb);
                 pbad |= (par & kSign) != 0;
@@ -241,13 +281,9 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
                 for (int i = tid; i < n_var; i += nth) {
                     const int jl = i / Z, c = i - jl * Z;
                     const int j = my_cols[jl];
-                    float sum = __ldg(L + j * Z + c);
-                    for (int e = t_colptr[j]; e < t_colptr[j + 1]; e++) {
-                        const int ce = t_cent[e];
-                        int rr = c - (ce >> 20);
-                        rr += (rr < 0) ? Z : 0;
-                        sum += (float)(t_cown[e] ? r_1 : r_0)[(ce & 0xfffff) + rr];
-                    }
+                    const int e0 = t_colptr[j];
+                    const float sum = cl_vn_column<MsgT>(t_colptr[j + 1] - e0, t_cd + e0, r_0, r_1, c, Z,
+                                                         __ldg(L + j * Z + c));
                     app[i] = sum + 0.0f;  // -0 -> +0: the sign bit is the decision
                 }
                 t++;
@@ -277,7 +313,6 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
 // ------------------------------------------------------------------ host side
 
 // bytes of the table area ahead of APP (the kernel's layout)
-static size_t cl_tables_bytes() { return (16 + 4 * (2 * NNZ_MAX + MB_MAX + NB_MAX + 2 + NNZ_MAX) + 15) & ~(size_t)15; }
 
 // Split the block rows between the cluster's CTAs in contiguous ranges of about equal block
 // counts, then give each block column to the CTA that owns most of its blocks' rows (its
@@ -318,7 +353,7 @@ static size_t cl_plan(const CodeDev &h, int msg, ClusterArgs &a, size_t limit)
         cnt[best]++;
     }
     // the posterior share of a CTA may not exceed what its shared memory has left
-    const size_t fixed = cl_tables_bytes() + nr * msz;
+    const size_t fixed = cl_tables_bytes(h.nnz) + nr * msz;
     const int cap = limit > fixed ? (int)((limit - fixed) / (4 * (size_t)h.Z)) : 0;
     for (int q = 0; q < CLUSTER_CTAS; q++) {
         while (cnt[q] > cap) {
@@ -343,7 +378,7 @@ static size_t cl_plan(const CodeDev &h, int msg, ClusterArgs &a, size_t limit)
     }
     int nmax = 0;
     for (int q = 0; q < CLUSTER_CTAS; q++) nmax = a.ncols[q] > nmax ? a.ncols[q] : nmax;
-    return cl_tables_bytes() + (((size_t)nmax * h.Z * 4 + 15) & ~(size_t)15) + nr * msz;
+    return cl_tables_bytes(h.nnz) + (((size_t)nmax * h.Z * 4 + 15) & ~(size_t)15) + nr * msz;
 }
 
 static size_t cl_limit()

@@ -210,6 +210,39 @@ __device__ __forceinline__ void lgroup_sync(int grp, int tpg)
         asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(tpg) : "memory");
 }
 
+// Parity of the hard decisions (APP < 0) of check row r of one block row (degree dc):
+// straight-line bodies for the common degrees (every lane of a warp takes the same branch).
+template <int D>
+__device__ __forceinline__ unsigned lslots_parity(const int2 *__restrict__ ed, const int8_t *A, int r, int Z)
+{
+    unsigned par = 0;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        const int2 d = ed[k];
+        par ^= A[r + d.x - (r >= d.y ? Z : 0)] < 0 ? 1u : 0u;
+    }
+    return par;
+}
+__device__ __forceinline__ unsigned lslots_row_parity(int dc, const int2 *__restrict__ ed, const int8_t *A, int r,
+                                                      int Z)
+{
+    switch (dc) {
+    case 4: return lslots_parity<4>(ed, A, r, Z);
+    case 5: return lslots_parity<5>(ed, A, r, Z);
+    case 6: return lslots_parity<6>(ed, A, r, Z);
+    case 7: return lslots_parity<7>(ed, A, r, Z);
+    case 8: return lslots_parity<8>(ed, A, r, Z);
+    default: {
+        unsigned par = 0;
+        for (int k = 0; k < dc; k++) {
+            const int2 d = ed[k];
+            par ^= A[r + d.x - (r >= d.y ? Z : 0)] < 0 ? 1u : 0u;
+        }
+        return par;
+    }
+    }
+}
+
 // Table space (ints) ahead of the slots: two per block for its edge descriptor, then the
 // block-row pointers.
 __host__ __device__ inline int lslots_tables_ints(int nnz, int mb) { return 2 * nnz + mb + 1; }
@@ -334,12 +367,8 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
         if (busy && a.early_exit) {
             unsigned par_any = 0;
             for (int l = 0; l < mb; l++) {
-                unsigned par = 0;
-                for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++) {
-                    const int2 d = t_ed[b];
-                    par ^= A[r + d.x - (r >= d.y ? Z : 0)] < 0 ? 1u : 0u;
-                }
-                par_any |= par;
+                const int b0 = t_rowptr[l];
+                par_any |= lslots_row_parity(t_rowptr[l + 1] - b0, t_ed + b0, A, r, Z);
             }
             if (par_any) bad[c] = 1;
         }

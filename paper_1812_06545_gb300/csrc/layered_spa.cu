@@ -178,6 +178,33 @@ __device__ __forceinline__ void layer_check_dispatch(int dc, const int4 *__restr
     }
 }
 
+// XOR of the posterior sign bits of check row r of one block row (degree dc): straight-line
+// bodies for the common degrees (every lane of a warp takes the same branch).
+template <int D>
+__device__ __forceinline__ uint32_t lspa_parity(const int4 *__restrict__ ed, const char *Ar, int r, int ZA)
+{
+    uint32_t par = 0;
+#pragma unroll
+    for (int k = 0; k < D; k++) par ^= __float_as_uint(*at<float>(Ar, lspa_app_off(ed[k], r, ZA)));
+    return par;
+}
+__device__ __forceinline__ uint32_t lspa_row_parity(int dc, const int4 *__restrict__ ed, const char *Ar, int r,
+                                                    int ZA)
+{
+    switch (dc) {
+    case 4: return lspa_parity<4>(ed, Ar, r, ZA);
+    case 5: return lspa_parity<5>(ed, Ar, r, ZA);
+    case 6: return lspa_parity<6>(ed, Ar, r, ZA);
+    case 7: return lspa_parity<7>(ed, Ar, r, ZA);
+    case 8: return lspa_parity<8>(ed, Ar, r, ZA);
+    default: {
+        uint32_t par = 0;
+        for (int k = 0; k < dc; k++) par ^= __float_as_uint(*at<float>(Ar, lspa_app_off(ed[k], r, ZA)));
+        return par;
+    }
+    }
+}
+
 // Table space (ints) ahead of the slots: four per block for its edge descriptor, then the
 // block-row pointers.
 __host__ __device__ inline int lspa_tables_ints(int nnz, int mb) { return 4 * nnz + mb + 1; }
@@ -283,10 +310,8 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
         if (busy && a.early_exit) {
             uint32_t par_any = 0;
             for (int l = 0; l < mb; l++) {
-                uint32_t par = 0;
-                for (int b = t_rowptr[l]; b < t_rowptr[l + 1]; b++)
-                    par ^= __float_as_uint(*at<float>(Ar, lspa_app_off(t_ed[b], r, ZA)));
-                par_any |= par;
+                const int b0 = t_rowptr[l];
+                par_any |= lspa_row_parity(t_rowptr[l + 1] - b0, t_ed + b0, Ar, r, ZA);
             }
             if (par_any & 0x80000000u) bad[c] = 1;
         }
