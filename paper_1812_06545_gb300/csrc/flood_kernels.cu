@@ -371,6 +371,26 @@ __global__ void __launch_bounds__(256, LDPC_CN_MINB) k_flood_cn(const CodeDev *_
 
 // ------------------------------------------------------------------ variable-node phase
 
+// Messages of D column entries (colent: (b << 16) | s) of variable position c, added onto s
+// in the order of the column lists; all D loads are issued before the first add.
+template <int D, int V, typename MsgT>
+__device__ __forceinline__ void svn_sum(const int32_t *__restrict__ colent, const MsgT *rt, int c, int Z,
+                                        float (&s)[V])
+{
+    float rv[D][V];
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        const int ce = colent[k];
+        int rr = c - (ce & 0xffff);
+        rr += (rr < 0) ? Z : 0;
+        Msg<MsgT, V>::load(rt + (int64_t)((ce >> 16) * Z + rr) * TILE, rv[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < D; k++)
+#pragma unroll
+        for (int v = 0; v < V; v++) s[v] += rv[k][v];
+}
+
 // One warp per (tile, variable n, lane group): APP_n = L_n + sum over the column's blocks
 // of R at edge (b, (c - s) mod Z), c = n mod Z.  Codewords already frozen keep their APP;
 // a codeword whose iteration-t check phase stamped no failing check is frozen here with
@@ -413,16 +433,15 @@ __global__ void __launch_bounds__(256) k_flood_vn(const CodeDev *__restrict__ cd
     float s[V];
     ld_f<V>(L + ((int64_t)tile * N + n) * TILE + slot, s);
     const MsgT *rt = R + (int64_t)tile * cd->E * TILE + slot;
-    const int i1 = cd->colptr[j + 1];
-    for (int i = cd->colptr[j]; i < i1; i++) {
-        const int ce = cd->colent[i];
-        int rr = c - (ce & 0xffff);
-        rr += (rr < 0) ? Z : 0;
-        float rv[V];
-        Msg<MsgT, V>::load(rt + (int64_t)((ce >> 16) * Z + rr) * TILE, rv);
-#pragma unroll
-        for (int v = 0; v < V; v++) s[v] += rv[v];
-    }
+    const int i0 = cd->colptr[j], dv = cd->colptr[j + 1] - i0;
+    if (dv == 3)
+        svn_sum<3, V, MsgT>(cd->colent + i0, rt, c, Z, s);
+    else if (dv == 2)
+        svn_sum<2, V, MsgT>(cd->colent + i0, rt, c, Z, s);
+    else if (dv == 4)
+        svn_sum<4, V, MsgT>(cd->colent + i0, rt, c, Z, s);
+    else
+        for (int i = 0; i < dv; i++) svn_sum<1, V, MsgT>(cd->colent + i0 + i, rt, c, Z, s);
 #pragma unroll
     for (int v = 0; v < V; v++) s[v] += 0.0f;  // -0 -> +0: the APP sign bit is the hard decision
     float *dst = app + ((int64_t)tile * N + n) * TILE + slot;
