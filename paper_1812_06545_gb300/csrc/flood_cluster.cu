@@ -70,7 +70,7 @@ __device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed
             par ^= __float_as_uint(ap);
             const uint32_t qs = __float_as_uint(qv) & kSign;
             sg ^= qs;
-            av[k] = __uint_as_float(__float_as_uint(fminf(s_psi_in(fminf(fabsf(qv), X)), Xb)) | qs);
+            av[k] = __uint_as_float(__float_as_uint(fminf(s_psi_in<false>(fminf(fabsf(qv), X)), Xb)) | qs);
         }
     }
     if constexpr (D <= 8) {
@@ -83,7 +83,7 @@ __device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed
 #pragma unroll
         for (int k = 0; k < D; k++) {
             if (EXACT || k < dc) {
-                const float mag = fminf(s_phi_out(pre + sf[k + 1]), X);
+                const float mag = fminf(s_phi_out<false>(pre + sf[k + 1]), X);
                 pre += fabsf(av[k]);
                 Rr[k * Z] = MsgT(__uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k]) ^ sg) & kSign)));
             }
@@ -106,7 +106,7 @@ __device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed
         for (int k = 0; k < D; k++) {
             if (EXACT || k < dc) {
                 const float ak = fabsf(av[k]);
-                const float mag = fminf(s_phi_out(ak == amax ? sx : S - ak), X);
+                const float mag = fminf(s_phi_out<false>(ak == amax ? sx : S - ak), X);
                 Rr[k * Z] = MsgT(__uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k]) ^ sg) & kSign)));
             }
         }

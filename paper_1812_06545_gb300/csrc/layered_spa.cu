@@ -23,12 +23,19 @@
 // checks; a slot that converged (early exit) or reached max_iter writes its outputs and
 // takes the next codeword from the global work counter at its group's next iteration.
 //
-// APP is never -0: the refill adds +0 to the channel value and Q + R' is -0 only when both
+// APP is never -0: the refill adds +0 to the (scaled) channel value and Q + R' is -0 only when both
 // are -0, which cannot happen while APP is not -0 (then Q = APP - R is not -0).  The sign
 // bit therefore is the hard decision [APP < 0] and sgn(0) = +1, as the oracle reads it.
 #include "slot_common.cuh"
 
 namespace ldpc {
+
+// The FP32-message form keeps APP, Q and R in base-2 units (LLR x log2 e, set at the refill
+// and undone at the output), which spares the phi evaluations their scaling multiplies; the
+// FP16-message form stays in natural units, so that its stored binary16 message is the
+// natural-unit value rounded, as the oracle's binary16 mode rounds it.
+template <typename MsgT>
+constexpr bool kBase2 = sizeof(MsgT) == 4;
 
 struct LayeredSpaArgs {
     const float *llr;
@@ -96,7 +103,7 @@ __device__ __forceinline__ void layer_check(int dc, const int4 *__restrict__ ed,
                 q[k] = *at<float>(Ar, ao[k]) - MsgIO<MsgT>::ld(Rl + k * Zm);
                 const uint32_t qs = __float_as_uint(q[k]) & kSign;
                 sg ^= qs;
-                a[k] = __uint_as_float(__float_as_uint(fminf(s_psi_in(fminf(fabsf(q[k]), X)), Xb)) | qs);
+                a[k] = __uint_as_float(__float_as_uint(fminf(s_psi_in<kBase2<MsgT>>(fminf(fabsf(q[k]), X)), Xb)) | qs);
             }
         }
         // exclusive sums from suffix and prefix sums (no cancellation)
@@ -108,7 +115,7 @@ __device__ __forceinline__ void layer_check(int dc, const int4 *__restrict__ ed,
 #pragma unroll
         for (int k = 0; k < D; k++) {
             if (EXACT || k < dc) {
-                const float mag = fminf(s_phi_out(pre + sf[k + 1]), X);
+                const float mag = fminf(s_phi_out<kBase2<MsgT>>(pre + sf[k + 1]), X);
                 pre += fabsf(a[k]);
                 const float out = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(a[k]) ^ sg) & kSign));
                 *at<float>(Ar, ao[k]) = q[k] + MsgIO<MsgT>::st(Rl + k * Zm, out);
@@ -130,7 +137,7 @@ __device__ __forceinline__ void layer_check(int dc, const int4 *__restrict__ ed,
                 const float q = *at<float>(Ar, oa) - MsgIO<MsgT>::ld(Rl + k * Zm);
                 const uint32_t qs = __float_as_uint(q) & kSign;
                 sg ^= qs;
-                const float m = fminf(s_psi_in(fminf(fabsf(q), X)), Xb);
+                const float m = fminf(s_psi_in<kBase2<MsgT>>(fminf(fabsf(q), X)), Xb);
                 a[k] = __uint_as_float(__float_as_uint(m) | qs);
                 S += m;
                 amax = fmaxf(amax, m);
@@ -145,7 +152,7 @@ __device__ __forceinline__ void layer_check(int dc, const int4 *__restrict__ ed,
         for (int k = 0; k < D; k++) {
             if (EXACT || k < dc) {
                 const float ak = fabsf(a[k]);
-                const float mag = fminf(s_phi_out(ak == amax ? sx : S - ak), X);
+                const float mag = fminf(s_phi_out<kBase2<MsgT>>(ak == amax ? sx : S - ak), X);
                 const float out = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(a[k]) ^ sg) & kSign));
                 int ai;
                 if constexpr (kHoldIdx)
@@ -245,7 +252,8 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
     MsgT *Rs = reinterpret_cast<MsgT *>(APPs + (size_t)C * a.strideA);
 
     const int tid = threadIdx.x, nth = blockDim.x;
-    const float X = a.X, Xb = a.X * kSLog2e;
+    // clamp X in the internal units (base-2 for FP32 messages); phi values are base-2 units
+    const float X = kBase2<MsgT> ? a.X * kSLog2e : a.X, Xb = a.X * kSLog2e;
     for (int i = tid; i < nnz; i += nth) {
         const int e = cd->ent[i], sh = e & 0xffff;
         t_ed[i] = make_int4((int)sizeof(float) * ((e >> 16) * Z + sh), (int)sizeof(MsgT) * i * Z, Z - sh, 0);
@@ -286,7 +294,7 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
         for (int j = 0; j < nb; j++) {
             const float v = __ldg(L + j * Z + r);
             if (!isfinite(v)) atomicOr(cd->status, IN_NONFINITE);
-            A[j * Z + r] = v + 0.0f;
+            A[j * Z + r] = kBase2<MsgT> ? fmaf(v, kSLog2e, 0.0f) : v + 0.0f;
         }
         for (int b = 0; b < nnz; b++) Rc[b * Z + r] = MsgT(0.0f);
     };
@@ -325,7 +333,7 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
                 for (int j = 0; j < nb; j++) {
                     const float v = A[j * Z + r];
                     Bo[j * Z + r] = v < 0.0f ? 1 : 0;
-                    if (Ao) Ao[j * Z + r] = v;
+                    if (Ao) Ao[j * Z + r] = kBase2<MsgT> ? v * kSLn2 : v;
                 }
                 if (r == 0) {
                     a.iters[cw] = t;

@@ -23,23 +23,40 @@ __device__ __forceinline__ float s_lg2(float x)
 constexpr float kSLog2e = 1.4426950408889634f;
 constexpr float kSLn2 = 0.6931471805599453f;
 
-// ln((1 + t)/(1 - t)) is evaluated as lg2(1 + t) - lg2(1 - t): the two logarithms are
-// independent (a shorter dependency chain than a reciprocal followed by one logarithm) and
-// have opposite signs, so their difference does not cancel.
+// The phi evaluations below take their argument in natural units, or in base-2 units
+// (LLR x log2 e) for a decoder that keeps APP, Q and R scaled (B2), where neither needs a
+// scaling multiply.
+
+// phi(x) in base-2 units for x = |Q| (already clamped), in base-2 units (B2) or natural
+// units.  ln((1 + t)/(1 - t)) is evaluated as lg2(1 + t) - lg2(1 - t): the two logarithms
+// are independent (a shorter dependency chain than a reciprocal followed by one logarithm)
+// and have opposite signs, so their difference does not cancel; for x above 3 (natural)
+// the series 2t + 2t^3/3 keeps the relative accuracy that the difference would lose.
+template <bool B2>
 __device__ __forceinline__ float s_psi_in(float x)
 {
-    const float t = s_ex2(-x * kSLog2e);
+    const float t = s_ex2(B2 ? -x : -x * kSLog2e);
     const float big = t * fmaf(t * t, (2.0f / 3.0f) * kSLog2e, 2.0f * kSLog2e);
     const float mid = s_lg2(1.0f + t) - s_lg2(1.0f - t);
-    return x > 3.0f ? big : mid;
+    return x > (B2 ? 4.328085f : 3.0f) ? big : mid;
 }
 
+// phi of a sum s2 given in base-2 units, returned in base-2 units (B2) or natural units.
+// 1 - e^-S is taken from its series below S = 1/16 (natural), where the difference would
+// cancel; in base-2 units the series coefficients carry the powers of ln 2.
+template <bool B2>
 __device__ __forceinline__ float s_phi_out(float s2)
 {
     const float t = s_ex2(-s2);
-    const float S = s2 * kSLn2;
-    const float den = S < 0.0625f ? S * fmaf(S, fmaf(S, 1.0f / 6.0f, -0.5f), 1.0f) : 1.0f - t;
-    return (s_lg2(1.0f + t) - s_lg2(den)) * kSLn2;
+    float den;
+    if constexpr (B2) {
+        den = s2 < 0.09016844f ? s2 * fmaf(s2, fmaf(s2, 0.05550411f, -0.2402265f), kSLn2) : 1.0f - t;
+        return s_lg2(1.0f + t) - s_lg2(den);
+    } else {
+        const float S = s2 * kSLn2;
+        den = S < 0.0625f ? S * fmaf(S, fmaf(S, 1.0f / 6.0f, -0.5f), 1.0f) : 1.0f - t;
+        return (s_lg2(1.0f + t) - s_lg2(den)) * kSLn2;
+    }
 }
 
 // V consecutive slots share each shared-memory element group: APP and R are laid out
@@ -132,7 +149,7 @@ __device__ __forceinline__ void slot_check(int dc, const int4 *__restrict__ ed, 
             for (int v = 0; v < V; v++) {
                 const float q = ap[v] - rv[v];
                 par[v] ^= __float_as_uint(ap[v]);
-                const float mag = fminf(s_psi_in(fminf(fabsf(q), X)), Xb);
+                const float mag = fminf(s_psi_in<false>(fminf(fabsf(q), X)), Xb);
                 const uint32_t qs = __float_as_uint(q) & kSign;
                 sg[v] ^= qs;
                 av[k][v] = __uint_as_float(__float_as_uint(mag) | qs);
@@ -157,7 +174,7 @@ __device__ __forceinline__ void slot_check(int dc, const int4 *__restrict__ ed, 
                 float out[V];
 #pragma unroll
                 for (int v = 0; v < V; v++) {
-                    const float mag = fminf(s_phi_out(pre[v] + sf[k + 1][v]), X);
+                    const float mag = fminf(s_phi_out<false>(pre[v] + sf[k + 1][v]), X);
                     pre[v] += fabsf(av[k][v]);
                     out[v] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
                 }
@@ -196,7 +213,7 @@ __device__ __forceinline__ void slot_check(int dc, const int4 *__restrict__ ed, 
 #pragma unroll
                 for (int v = 0; v < V; v++) {
                     const float ak = fabsf(av[k][v]);
-                    const float mag = fminf(s_phi_out(ak == amax[v] ? sx[v] : S[v] - ak), X);
+                    const float mag = fminf(s_phi_out<false>(ak == amax[v] ? sx[v] : S[v] - ak), X);
                     out[v] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
                 }
                 SMsg<MsgT, V>::st(at<MsgT>(Rr, xo[k]), out);
@@ -212,29 +229,41 @@ __device__ __forceinline__ void slot_check(int dc, const int4 *__restrict__ ed, 
 // FFMA2 on sm_100+); the special functions, min/max, selects and sign-bit logic stay scalar.
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
+template <bool B2>
 __device__ __forceinline__ float2 psi_in2(float2 x)
 {
-    const float2 arg = __fmul2_rn(x, f2(-kSLog2e, -kSLog2e));
+    float2 arg = f2(-x.x, -x.y);
+    if constexpr (!B2) arg = __fmul2_rn(x, f2(-kSLog2e, -kSLog2e));
     const float2 t = f2(s_ex2(arg.x), s_ex2(arg.y));
     const float2 big = __fmul2_rn(t, __ffma2_rn(__fmul2_rn(t, t), f2((2.0f / 3.0f) * kSLog2e, (2.0f / 3.0f) * kSLog2e),
                                                 f2(2.0f * kSLog2e, 2.0f * kSLog2e)));
     const float2 num = __fadd2_rn(t, f2(1.0f, 1.0f));
     const float2 den = __ffma2_rn(t, f2(-1.0f, -1.0f), f2(1.0f, 1.0f));
     const float2 mid = __fadd2_rn(f2(s_lg2(num.x), s_lg2(num.y)), f2(-s_lg2(den.x), -s_lg2(den.y)));
-    return f2(x.x > 3.0f ? big.x : mid.x, x.y > 3.0f ? big.y : mid.y);
+    constexpr float th = B2 ? 4.328085f : 3.0f;
+    return f2(x.x > th ? big.x : mid.x, x.y > th ? big.y : mid.y);
 }
 
+template <bool B2>
 __device__ __forceinline__ float2 phi_out2(float2 s2)
 {
     const float2 t = f2(s_ex2(-s2.x), s_ex2(-s2.y));
-    const float2 S = __fmul2_rn(s2, f2(kSLn2, kSLn2));
-    const float2 poly = __fmul2_rn(S, __ffma2_rn(S, __ffma2_rn(S, f2(1.0f / 6.0f, 1.0f / 6.0f), f2(-0.5f, -0.5f)),
-                                                 f2(1.0f, 1.0f)));
     const float2 omt = __ffma2_rn(t, f2(-1.0f, -1.0f), f2(1.0f, 1.0f));
-    const float2 den = f2(S.x < 0.0625f ? poly.x : omt.x, S.y < 0.0625f ? poly.y : omt.y);
     const float2 num = __fadd2_rn(t, f2(1.0f, 1.0f));
-    const float2 d = __fadd2_rn(f2(s_lg2(num.x), s_lg2(num.y)), f2(-s_lg2(den.x), -s_lg2(den.y)));
-    return __fmul2_rn(d, f2(kSLn2, kSLn2));
+    if constexpr (B2) {
+        const float2 poly = __fmul2_rn(
+            s2, __ffma2_rn(s2, __ffma2_rn(s2, f2(0.05550411f, 0.05550411f), f2(-0.2402265f, -0.2402265f)),
+                           f2(kSLn2, kSLn2)));
+        const float2 den = f2(s2.x < 0.09016844f ? poly.x : omt.x, s2.y < 0.09016844f ? poly.y : omt.y);
+        return __fadd2_rn(f2(s_lg2(num.x), s_lg2(num.y)), f2(-s_lg2(den.x), -s_lg2(den.y)));
+    } else {
+        const float2 S = __fmul2_rn(s2, f2(kSLn2, kSLn2));
+        const float2 poly = __fmul2_rn(S, __ffma2_rn(S, __ffma2_rn(S, f2(1.0f / 6.0f, 1.0f / 6.0f), f2(-0.5f, -0.5f)),
+                                                     f2(1.0f, 1.0f)));
+        const float2 den = f2(S.x < 0.0625f ? poly.x : omt.x, S.y < 0.0625f ? poly.y : omt.y);
+        const float2 d = __fadd2_rn(f2(s_lg2(num.x), s_lg2(num.y)), f2(-s_lg2(den.x), -s_lg2(den.y)));
+        return __fmul2_rn(d, f2(kSLn2, kSLn2));
+    }
 }
 
 template <int D, bool EXACT, typename MsgT>
@@ -256,7 +285,7 @@ __device__ __forceinline__ void slot_check_pair(int dc, const int4 *__restrict__
             const float2 q = __ffma2_rn(f2(rv[0], rv[1]), f2(-1.0f, -1.0f), f2(ap[0], ap[1]));
             par0 ^= __float_as_uint(ap[0]);
             par1 ^= __float_as_uint(ap[1]);
-            const float2 m = psi_in2(f2(fminf(fabsf(q.x), X), fminf(fabsf(q.y), X)));
+            const float2 m = psi_in2<false>(f2(fminf(fabsf(q.x), X), fminf(fabsf(q.y), X)));
             const uint32_t qs0 = __float_as_uint(q.x) & kSign, qs1 = __float_as_uint(q.y) & kSign;
             sg0 ^= qs0;
             sg1 ^= qs1;
@@ -274,7 +303,7 @@ __device__ __forceinline__ void slot_check_pair(int dc, const int4 *__restrict__
 #pragma unroll
         for (int k = 0; k < D; k++) {
             if (EXACT || k < dc) {
-                const float2 mag = phi_out2(__fadd2_rn(pre, sf[k + 1]));
+                const float2 mag = phi_out2<false>(__fadd2_rn(pre, sf[k + 1]));
                 const float2 aa = f2(fabsf(av[k].x), fabsf(av[k].y));
                 pre = __fadd2_rn(pre, aa);
                 float out[2];
@@ -306,7 +335,7 @@ __device__ __forceinline__ void slot_check_pair(int dc, const int4 *__restrict__
         for (int k = 0; k < D; k++) {
             if (EXACT || k < dc) {
                 const float a0 = fabsf(av[k].x), a1 = fabsf(av[k].y);
-                const float2 mag = phi_out2(f2(a0 == m0 ? x0 : S.x - a0, a1 == m1 ? x1 : S.y - a1));
+                const float2 mag = phi_out2<false>(f2(a0 == m0 ? x0 : S.x - a0, a1 == m1 ? x1 : S.y - a1));
                 float out[2];
                 out[0] = __uint_as_float(__float_as_uint(fminf(mag.x, X)) | ((__float_as_uint(av[k].x) ^ sg0) & kSign));
                 out[1] = __uint_as_float(__float_as_uint(fminf(mag.y, X)) | ((__float_as_uint(av[k].y) ^ sg1) & kSign));
