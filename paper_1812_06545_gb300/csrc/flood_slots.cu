@@ -85,6 +85,9 @@ __device__ __forceinline__ void vn_column(int dv, const int32_t *__restrict__ ce
         }
 }
 
+// Barrier groups of a CTA: named barriers 1..15 (barrier 0 is the CTA's).
+constexpr int FLOOD_GROUPS_MAX = 15;
+
 template <int DMAX, int V, typename MsgT>
 __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const __grid_constant__ FloodMultiArgs a)
 {
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
     int32_t *bad = reinterpret_cast<int32_t *>(smem);            // [SLOTS_MAX] unsatisfied check seen this round
     int32_t *sreq = bad + SLOTS_MAX;                             // [SLOTS_MAX] request of the next codeword
     int64_t *fresh = reinterpret_cast<int64_t *>(sreq + SLOTS_MAX);  // [SLOTS_MAX] next codeword (request-local)
-    int32_t *misc = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);  // [4] group hand-over
+    int32_t *misc = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);  // [4] code-group hand-over
     int4 *t_ed = reinterpret_cast<int4 *>(misc + 4);  // 16-byte aligned: the head is a multiple of 16 bytes
     float *APPs = reinterpret_cast<float *>(smem + slots_smem_head(a.tbl_ints));
 
@@ -130,8 +133,15 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
         }
         for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
         for (int i = tid; i <= nb; i += nth) t_colptr[i] = cd->colptr[i];
-        const int g = tid / Z, r = tid - (tid / Z) * Z;
-        const bool mine = g < G;
+        // barrier group bg of this thread (paired slots, V = 2): K thread slots whose K*Z rows
+        // are packed into TPG threads (whole warps); thread u of the group owns row u mod Z of
+        // thread slot bg*K + u / Z.  Single slots (V = 1) run as one lock-step group of the
+        // whole CTA: thread tid owns row tid mod Z of thread slot tid / Z.
+        const int K = V == 2 ? gd.K : G, TPG = V == 2 ? gd.TPG : nth;
+        const int bg = V == 2 ? tid / TPG : 0, u = V == 2 ? tid - bg * TPG : tid;
+        const int g = bg * K + u / Z, r = u - (u / Z) * Z;
+        const bool mine = g < G && (V == 1 || u < K * Z);
+        const bool member = bg * K < G;  // the group has slots (else whole idle warps)
 
         // a slot's leader takes the group's next codeword and finds its request
         auto grab = [&](int s) {
@@ -193,13 +203,39 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
             }
         };
 
+        // the barrier of this thread's group, and the barrier that also returns the OR of a
+        // predicate over the group (bar.red: a reduction on a named barrier)
+        auto gsync = [&]() {
+            if constexpr (V == 1)
+                __syncthreads();
+            else if (TPG == 32)
+                __syncwarp();
+            else
+                asm volatile("bar.sync %0, %1;" ::"r"(bg + 1), "r"(TPG) : "memory");
+        };
+        auto group_any = [&](bool pred) -> bool {
+            if constexpr (V == 1) return __syncthreads_or(pred) != 0;
+            if (TPG == 32) {
+                __syncwarp();
+                return __any_sync(0xffffffffu, pred);
+            }
+            int any_set;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+                "selp.u32 %0, 1, 0, q;\n\t}"
+                : "=r"(any_set)
+                : "r"((unsigned)pred), "r"(bg + 1), "r"(TPG)
+                : "memory");
+            return any_set != 0;
+        };
+
         bool any = false;
 #pragma unroll
         for (int v = 0; v < V; v++) {
             if (cw[v] >= 0) refill(v);
             any |= cw[v] >= 0;
         }
-        any = __syncthreads_or(any);
+        any = V == 1 ? __syncthreads_or(any) != 0 : member && group_any(any);
 
         while (any) {
             // ---------------- check-node phase: row r of every block row, all V slots at once
@@ -215,7 +251,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                 for (int v = 0; v < V; v++)
                     if (cw[v] >= 0 && (pbad[v] & kSign)) bad[g * V + v] = 1;
             }
-            __syncthreads();
+            gsync();
 
             // ---------------- decision, variable-node phase, output
             bool done[V];
@@ -275,7 +311,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                     }
                 }
             }
-            __syncthreads();
+            gsync();
 
             // ---------------- refill finished slots
             any = false;
@@ -292,7 +328,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                     any |= cw[v] >= 0;
                 }
             }
-            any = __syncthreads_or(any);
+            any = group_any(any);
         }
 
         // this group is dry here and every slot has drained: move to the group with the
@@ -476,7 +512,22 @@ cudaError_t flood_multi_decode(const HostReq *reqs, int n, const ldpc_decode_par
         gd.n_items = items;
         const size_t sm = slots_smem_head(tbl) + slots_bytes(h, p.msg, gd.C);
         smem = sm > smem ? sm : smem;
-        const int th = ((gd.C / V * h.Z + 31) / 32) * 32;
+        // barrier groups (paired slots): the smallest group of thread slots whose whole-warp
+        // groups need no more threads than one lock-step group of all of them (the idle lanes
+        // of a group are only those of its last warp); one group when none does, and always
+        // for single slots
+        const int G = gd.C / V, t0 = ((G * h.Z + 31) / 32) * 32;
+        gd.K = G;
+        gd.TPG = t0;
+        for (int k = 1; V == 2 && k < G; k++) {
+            const int tp = ((k * h.Z + 31) / 32) * 32, ng = (G + k - 1) / k;
+            if (ng <= FLOOD_GROUPS_MAX && ng * tp <= t0) {
+                gd.K = k;
+                gd.TPG = tp;
+                break;
+            }
+        }
+        const int th = ((G + gd.K - 1) / gd.K) * gd.TPG;
         threads = th > threads ? th : threads;
         wsum += (double)items * h.E;
         min_ctas += (items + gd.C - 1) / gd.C;

@@ -91,7 +91,8 @@ struct ReqDev {
 };
 struct GroupDev {
     const CodeDev *code;
-    int C;  // slots per CTA for this code
+    int C;       // slots per CTA for this code
+    int K, TPG;  // thread slots per barrier group; threads per group (whole warps)
     int req_begin, req_end;
     int N, E, Z, mb, nb, nnz, dc_max;
     int64_t n_items;
