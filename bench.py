@@ -23,6 +23,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -155,7 +156,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples (the JSON line carries their summary); LDPC_CLOCKS_DIR keeps them
+        out = os.environ.get("LDPC_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"ldpc_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
