@@ -109,6 +109,32 @@ def test_batch_invariance(cuda_dev, form):
         assert np.array_equal(app1[0], app_all[i]) and it1[0] == it_all[i]
 
 
+@pytest.mark.parametrize("name,slots,eb", [("qc16x32_z32_s7", 20, 2.0), ("qc12x24_z24_s6", 40, 2.0),
+                                            ("qc12x24_z81_s2", 12, 1.75)])
+def test_paired_slots_in_barrier_groups(cuda_dev, name, slots, eb):
+    # A batch that fills every CTA's FP16 slots, so that the paired slots run in independent
+    # barrier groups: one-warp groups for Z = 32, groups of four thread slots in three whole
+    # warps for Z = 24, two groups of three for Z = 81.  Batches of two codewords per SM
+    # run one group per CTA.  Every codeword's arithmetic is its own, so the grouped decode
+    # must equal, bit for bit, the decode of the same codewords in such small batches (early
+    # exit on: slots finish at different iterations and refill at different times).  The
+    # first iteration also follows the FP16-message oracle on every codeword.
+    n = 152 * slots
+    _, _, c, L = I.make_frames(name, n, eb, 71, 72)
+    oc = oracle_code(name)
+    app, _, _ = run(name, "flood_f16", L, cuda_dev, max_iter=1, early_exit=0)
+    ref, _, _, R = oc.spa_flood(L, 1, early_exit=False, fp16_msgs=True, return_messages=True)
+    tol = FP32_TOL * np.maximum(1.0, np.abs(ref)) + 4 * 2.0 ** -11 * oc.incoming_message_sum(R)
+    assert (np.abs(app - ref) <= tol).all(), name
+    app_all, bits_all, it_all = run(name, "flood_f16", L, cuda_dev, max_iter=20, early_exit=1)
+    assert len(np.unique(it_all)) > 1  # codewords finish at different iterations
+    chunk = 2 * 152
+    for a in range(0, n, chunk):
+        app1, bits1, it1 = run(name, "flood_f16", L[a:a + chunk].copy(), cuda_dev, max_iter=20, early_exit=1)
+        assert np.array_equal(app1, app_all[a:a + chunk]), (name, a)
+        assert np.array_equal(bits1, bits_all[a:a + chunk]) and np.array_equal(it1, it_all[a:a + chunk])
+
+
 def test_small_and_empty_batches(cuda_dev):
     name = "qc12x24_z27_s1"
     code = gpu_code(name)
