@@ -21,9 +21,15 @@
 //                      takes the next codeword index from the global work counter
 //   barrier
 //   refill             a slot given a new codeword loads APP = L and clears its R
-//   barrier (with the CTA-wide "any slot busy" vote)
+//   barrier (with the "any slot busy" vote)
 // Codewords therefore leave as soon as they converge and free slots are refilled at once:
 // early exit saves whole rounds of work instead of idling lanes of a tile.
+//
+// Single slots (one codeword per thread) run the rounds in lock-step over the whole CTA.
+// Paired slots (two codewords per thread) run them in barrier groups: a group's thread slots
+// have their rows packed into whole warps and synchronise on their own named barrier, so
+// the groups of a CTA run their rounds independently; the host forms groups only where
+// they need no more warps than one lock-step group.
 //
 // One launch serves several requests (mixed codes): requests of the same code form a
 // group with its own work counter; each CTA starts on a group chosen in proportion to the
