@@ -59,6 +59,31 @@ struct FloodMultiArgs {
     float X;
 };
 
+// The check-node phase of one thread: row r of every block row, one loop per degree up to 8
+// over the rows of that degree (exact bodies, no per-row dispatch), then the rows above
+// degree 8 through the bucketed dispatch.  Flooding checks are independent, so the order of
+// the rows changes no result.
+template <int D, int DMAX, int V, typename MsgT>
+__device__ __forceinline__ void cn_rows(const int32_t *t_rord, const int32_t *t_dbeg, const int32_t *t_rowptr,
+                                        const int4 *__restrict__ t_ed, const char *Ar, char *Rr, int r, int ZA,
+                                        int ZR, float X, float Xb, uint32_t (&pbad)[V])
+{
+    if constexpr (D <= 8) {
+        if constexpr (D <= DMAX) {
+            const int i1 = t_dbeg[D - 1];
+            for (int i = t_dbeg[D - 2]; i < i1; i++)
+                slot_check_v<D, true, V, MsgT>(D, t_ed + t_rowptr[t_rord[i]], Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+        }
+        cn_rows<D + 1, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+    } else if constexpr (DMAX > 8) {
+        const int i1 = t_dbeg[8];
+        for (int i = t_dbeg[7]; i < i1; i++) {
+            const int l = t_rord[i], b0 = t_rowptr[l];
+            slot_check_dispatch<12, DMAX, V, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+        }
+    }
+}
+
 // Sum of the messages of one variable (column degree dv, message offsets ce) into sacc, in
 // the order of the column lists.  The common degrees get straight-line bodies; every lane
 // of a warp takes the same branch (a warp covers one block column).
@@ -139,6 +164,21 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
         }
         for (int i = tid; i <= mb; i += nth) t_rowptr[i] = cd->rowptr[i];
         for (int i = tid; i <= nb; i += nth) t_colptr[i] = cd->colptr[i];
+        // block rows ordered by degree (the check-node phase runs one loop per degree up to 8,
+        // so that a row needs no degree dispatch): t_rord[t_dbeg[d - 2] .. t_dbeg[d - 1]) are
+        // the rows of degree d, t_rord[t_dbeg[7] .. mb) those above degree 8
+        int32_t *t_rord = t_colptr + nb + 1, *t_dbeg = t_rord + mb;
+        if (tid == 0) {
+            int n = 0;
+            for (int d = 2; d <= 9; d++) {
+                t_dbeg[d - 2] = n;
+                for (int l = 0; l < mb; l++) {
+                    const int dl = cd->rowptr[l + 1] - cd->rowptr[l];
+                    if (d < 9 ? dl == d : dl > 8) t_rord[n++] = l;
+                }
+            }
+            t_dbeg[8] = n;
+        }
         // barrier group bg of this thread (paired slots, V = 2): K thread slots whose K*Z rows
         // are packed into TPG threads (whole warps); thread u of the group owns row u mod Z of
         // thread slot bg*K + u / Z.  Single slots (V = 1) run as one lock-step group of the
@@ -249,10 +289,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                 uint32_t pbad[V];
 #pragma unroll
                 for (int v = 0; v < V; v++) pbad[v] = 0;
-                for (int l = 0; l < mb; l++) {
-                    const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
-                    slot_check_dispatch<2, DMAX, V, MsgT>(dc, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
-                }
+                cn_rows<2, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
 #pragma unroll
                 for (int v = 0; v < V; v++)
                     if (cw[v] >= 0 && (pbad[v] & kSign)) bad[g * V + v] = 1;
@@ -383,7 +420,7 @@ static size_t max_smem_optin()
     return v > 0 ? (size_t)v : 227 * 1024;
 }
 
-static int tables_ints(const CodeDev &h) { return 5 * h.nnz + h.mb + 1 + h.nb + 1; }
+static int tables_ints(const CodeDev &h) { return 5 * h.nnz + h.mb + 1 + h.nb + 1 + h.mb + 9; }
 
 // Shared memory of C slots of a code: the APP region (16-byte aligned end) and the messages.
 static size_t slots_bytes(const CodeDev &h, int msg, int C)
