@@ -168,17 +168,8 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
         // so that a row needs no degree dispatch): t_rord[t_dbeg[d - 2] .. t_dbeg[d - 1]) are
         // the rows of degree d, t_rord[t_dbeg[7] .. mb) those above degree 8
         int32_t *t_rord = t_colptr + nb + 1, *t_dbeg = t_rord + mb;
-        if (tid == 0) {
-            int n = 0;
-            for (int d = 2; d <= 9; d++) {
-                t_dbeg[d - 2] = n;
-                for (int l = 0; l < mb; l++) {
-                    const int dl = cd->rowptr[l + 1] - cd->rowptr[l];
-                    if (d < 9 ? dl == d : dl > 8) t_rord[n++] = l;
-                }
-            }
-            t_dbeg[8] = n;
-        }
+        for (int i = tid; i < mb; i += nth) t_rord[i] = cd->rord[i];
+        for (int i = tid; i < 9; i += nth) t_dbeg[i] = cd->dbeg[i];
         // barrier group bg of this thread (paired slots, V = 2): K thread slots whose K*Z rows
         // are packed into TPG threads (whole warps); thread u of the group owns row u mod Z of
         // thread slot bg*K + u / Z.  Single slots (V = 1) run as one lock-step group of the

@@ -213,6 +213,17 @@ ldpc_status ldpc_code_create(const int32_t *base, int32_t mb, int32_t nb, int32_
             if ((h.ent[b] >> 16) == j) h.colent[k++] = (b << 16) | (h.ent[b] & 0xffff);
     }
     h.colptr[nb] = k;
+    {
+        int n = 0;
+        for (int d = 2; d <= 9; d++) {
+            h.dbeg[d - 2] = n;
+            for (int l = 0; l < mb; l++) {
+                const int dl = h.rowptr[l + 1] - h.rowptr[l];
+                if (d < 9 ? dl == d : dl > 8) h.rord[n++] = l;
+            }
+        }
+        h.dbeg[8] = n;
+    }
     h.nnz = nnz;
     h.N = nb * Z;
     h.M = mb * Z;

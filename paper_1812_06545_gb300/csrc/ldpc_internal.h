@@ -30,6 +30,10 @@ struct CodeDev {
     int32_t colptr[NB_MAX + 1];  // entries of block column j: [colptr[j], colptr[j+1])
     int32_t colent[NNZ_MAX];     // (b << 16) | s for those blocks
     unsigned int *status;        // the device's input status word (library-owned, one per device)
+    // block rows by degree: rord[dbeg[d - 2] .. dbeg[d - 1]) are the rows of degree d (2..8),
+    // rord[dbeg[7] .. dbeg[8]) those above degree 8 (for the flooding slot decoder)
+    int32_t rord[MB_MAX];
+    int32_t dbeg[12];
 };
 
 // Bits of the input status word: kernels that load channel LLRs set them (atomicOr, only
