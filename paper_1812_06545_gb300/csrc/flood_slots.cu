@@ -59,10 +59,10 @@ struct FloodMultiArgs {
     float X;
 };
 
-// The check-node phase of one thread: row r of every block row, one loop per degree up to 8
-// over the rows of that degree (exact bodies, no per-row dispatch), then the rows above
-// degree 8 through the bucketed dispatch.  Flooding checks are independent, so the order of
-// the rows changes no result.
+// The check-node phase of one thread for codes of row degree <= 8: row r of every block row,
+// one loop per degree over the rows of that degree (exact bodies, no per-row dispatch; the
+// branch above degree 8 serves wider instances).  Flooding checks are independent, so the
+// order of the rows changes no result.
 template <int D, int DMAX, int V, typename MsgT>
 __device__ __forceinline__ void cn_rows(const int32_t *t_rord, const int32_t *t_dbeg, const int32_t *t_rowptr,
                                         const int4 *__restrict__ t_ed, const char *Ar, char *Rr, int r, int ZA,
@@ -280,7 +280,16 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                 uint32_t pbad[V];
 #pragma unroll
                 for (int v = 0; v < V; v++) pbad[v] = 0;
-                cn_rows<2, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+                if constexpr (DMAX == 8) {
+                    cn_rows<2, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+                } else {
+                    // codes with rows above degree 8: per-row dispatch in row order (measured
+                    // faster here than the per-degree loops on the mixed-code launch)
+                    for (int l = 0; l < mb; l++) {
+                        const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
+                        slot_check_dispatch<2, DMAX, V, MsgT>(dc, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+                    }
+                }
 #pragma unroll
                 for (int v = 0; v < V; v++)
                     if (cw[v] >= 0 && (pbad[v] & kSign)) bad[g * V + v] = 1;
