@@ -190,6 +190,36 @@ def pin_spa_degree2(O):
     assert np.allclose(app, np.stack([s, s], axis=1), rtol=1e-11, atol=1e-11)
 
 
+def pin_spa_erasure_readings(O):
+    # an erased input (L = 0) at a degree-3 check, first iteration, both schedules.  Readings:
+    # sgn(0) = +1, and |Q| is clamped from below to phi(X) before phi, so an erasure
+    # contributes phi(phi(X)) = X to a check's sum instead of an infinite phi(0).
+    #  * toward the erased variable: the tanh rule on the other two, 2 atanh(tanh(a/2) tanh(b/2));
+    #  * toward the others: the sign of the other non-erased input (times +1 for the erasure)
+    #    and a magnitude that the erasure's X pushes down to at most phi(X) ~ 2 e^-X, but
+    #    not to zero.
+    a, b, X = 2.5, -1.5, 80.0
+    L = np.array([[0.0, a, b]], np.float32)
+    H = np.array([[1, 1, 1]], np.uint8)
+    code = O.Code.from_dense(H, layers=_per_check_layers(H))
+    tiny = 2.0 * np.exp(-X) * (1.0 + 1e-9)
+    for run in (code.spa_flood, code.spa_layered):
+        _, _, _, R = run(L, 1, early_exit=False, X=X, return_messages=True)
+        r0, r1, r2 = R[0]
+        want0 = 2.0 * np.arctanh(np.tanh(a / 2.0) * np.tanh(b / 2.0))
+        assert abs(r0 - want0) <= 1e-12 * abs(want0), (run.__name__, r0, want0)
+        assert -tiny <= r1 < 0.0, (run.__name__, r1)   # sign of b; erasure counts +1
+        assert 0.0 < r2 <= tiny, (run.__name__, r2)    # sign of a
+    # an erasure at each of two checks of a degree-2 variable stays an erasure for that check
+    # only: the other check still passes its degree-2 partner's value unchanged
+    H2 = np.array([[1, 1, 0], [0, 1, 1]], np.uint8)
+    code2 = O.Code.from_dense(H2, layers=_per_check_layers(H2))
+    L2 = np.array([[0.0, 0.0, 3.0]], np.float32)
+    app, _, _ = code2.spa_flood(L2, 1, early_exit=False, X=X)
+    assert abs(app[0, 1] - 3.0) <= 1e-12 * 3.0, app         # from check 1; check 0 adds ~phi(X)
+    assert 0.0 < app[0, 0] <= tiny, app                     # from check 0: the erased partner
+
+
 def pin_spa_tree_map(O):
     rng = np.random.default_rng(7)
     for trial in range(12):

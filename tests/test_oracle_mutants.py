@@ -57,6 +57,17 @@ MUTANTS = [
     ("binary16_precision", "int q = e - 11;", "int q = e - 10;", 0),
     ("ml_correlation_sign", "corr += ((cb[i] >> n) & 1u) ? -(double)Lb[n] : (double)Lb[n];",
      "corr += ((cb[i] >> n) & 1u) ? (double)Lb[n] : -(double)Lb[n];", 0),
+    # readings at an erased input (Q = 0): the lower clamp and sgn(0) = +1, both schedules
+    ("spa_no_lower_clamp", "if (a < phiX) a = phiX;", "", 0),
+    ("spa_sign_of_zero", "if (Q[k2] < 0.0) sgn = -sgn;", "if (Q[k2] <= 0.0) sgn = -sgn;", 0),
+    ("spal_no_lower_clamp", "if (a < phiX) a = phiX;", "", 1),
+    ("spal_sign_of_zero", "if (Q[k2] < 0.0) sgn = -sgn;", "if (Q[k2] <= 0.0) sgn = -sgn;", 1),
+    ("spa_messages_not_kept", "for (int e = 0; e < E; e++) R[e] = Rn[e];", "", 0),
+    ("spa_channel_doubled", "for (int n = 0; n < N; n++) app[n] = (double)Lb[n];\n                    for (int m = 0;",
+     "for (int n = 0; n < N; n++) app[n] = 2.0 * (double)Lb[n];\n                    for (int m = 0;", 0),
+    ("syndrome_or_not_xor", "for (int e = rp[m]; e < rp[m + 1]; e++) par ^= c[ci[e]] & 1;",
+     "for (int e = rp[m]; e < rp[m + 1]; e++) par |= c[ci[e]] & 1;", 0),
+    ("nms_min1_never_set", "if (a < min1) {", "if (0) {", 0),
 ]
 
 
