@@ -65,6 +65,27 @@ def test_fp16_messages_first_three_iterations(cuda_dev, form, name, n, eb):
         assert (d <= tol).all(), (name, T, (d - tol).max())
 
 
+@pytest.mark.parametrize("form", ["flood_f32", "stream_f32", "plain_f32", "layered_f32"])
+def test_erased_inputs(cuda_dev, form):
+    # 10 % of the LLRs erased (exactly 0, some of them -0.0): a zero |Q| is clamped up to
+    # phi(X) and counts as positive, so the check's other messages are at most phi(X) ~ 4e-35
+    # (0 in FP32); iterations 1-3 within the FP32 tolerance of the oracle, no NaN anywhere
+    name = "qc12x24_z81_s2"
+    _, _, c, L = I.make_frames(name, 300, 2.5, 81, 82)
+    rng = np.random.default_rng(83)
+    er = rng.random(L.shape) < 0.1
+    L[er] = 0.0
+    L[er & (rng.random(L.shape) < 0.5)] = -0.0
+    oc = oracle_code(name)
+    for T in (1, 2, 3):
+        app, _, _ = run(name, form, L, cuda_dev, max_iter=T, early_exit=0)
+        assert np.isfinite(app).all(), (form, T)
+        orc = oc.spa_layered if form.startswith("layered") else oc.spa_flood
+        ref, _, _ = orc(L, T, early_exit=False)
+        err = rel_err(app, ref)
+        assert err.max() <= FP32_TOL, (form, T, err.max())
+
+
 @pytest.mark.parametrize("form", ["flood_f32", "flood_f16", "stream_f32", "stream_f16", "plain_f32"])
 def test_early_exit_and_fer_full_size(cuda_dev, form):
     # 8192 codewords of the rate-1/2 N=1944 code, early exit, max 20 iterations, at 1.5
