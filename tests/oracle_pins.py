@@ -218,6 +218,13 @@ def pin_spa_erasure_readings(O):
     app, _, _ = code2.spa_flood(L2, 1, early_exit=False, X=X)
     assert abs(app[0, 1] - 3.0) <= 1e-12 * 3.0, app         # from check 1; check 0 adds ~phi(X)
     assert 0.0 < app[0, 0] <= tiny, app                     # from check 0: the erased partner
+    # a check of 11 erasures: each message is phi(10 X), which is 0 in double precision
+    # (e^-800 underflows), so every posterior stays exactly 0 and decides 0 (R1: APP = 0 -> 0)
+    H3 = np.ones((1, 11), np.uint8)
+    code3 = O.Code.from_dense(H3, layers=_per_check_layers(H3))
+    for run in (code3.spa_flood, code3.spa_layered):
+        app3, bits3, _ = run(np.zeros((1, 11), np.float32), 1, early_exit=False, X=X)
+        assert (app3 == 0.0).all() and (bits3 == 0).all(), (run.__name__, app3, bits3)
 
 
 def pin_spa_tree_map(O):

@@ -68,6 +68,12 @@ MUTANTS = [
     ("syndrome_or_not_xor", "for (int e = rp[m]; e < rp[m + 1]; e++) par ^= c[ci[e]] & 1;",
      "for (int e = rp[m]; e < rp[m + 1]; e++) par |= c[ci[e]] & 1;", 0),
     ("nms_min1_never_set", "if (a < min1) {", "if (0) {", 0),
+    # a posterior of exactly 0 decides 0 (R1), in all three decoders; a tie at the minimum
+    # leaves min2 = min1
+    ("spa_hd_zero_is_one", "hd[n] = app[n] < 0.0;", "hd[n] = app[n] <= 0.0;", 0),
+    ("spal_hd_zero_is_one", "hd[n] = app[n] < 0.0;", "hd[n] = app[n] <= 0.0;", 1),
+    ("nms_hd_zero_is_one", "hd[n] = app[n] < 0;", "hd[n] = app[n] <= 0;", 0),
+    ("nms_min2_skips_tie", "} else if (a < min2) {", "} else if (a < min2 && a != min1) {", 0),
 ]
 
 
