@@ -74,6 +74,15 @@ MUTANTS = [
     ("spal_hd_zero_is_one", "hd[n] = app[n] < 0.0;", "hd[n] = app[n] <= 0.0;", 1),
     ("nms_hd_zero_is_one", "hd[n] = app[n] < 0;", "hd[n] = app[n] <= 0;", 0),
     ("nms_min2_skips_tie", "} else if (a < min2) {", "} else if (a < min2 && a != min1) {", 0),
+    # binary16 message storage and the exclusive magnitude sum of the flooding routine
+    ("spa_fp16_ignored", "Rn[e0 + k] = fp16_msgs ? round_binary16(r) : r;", "Rn[e0 + k] = r;", 0),
+    ("binary16_round_away", "double r = nearbyint(ldexp(a, -q));", "double r = round(ldexp(a, -q));", 0),
+    ("binary16_no_subnormal_floor", "if (q < -24) q = -24;", "", 0),
+    ("binary16_overflow_threshold", "if (a >= 65520.0) return copysign(INFINITY, x);",
+     "if (a > 65504.0) return copysign(INFINITY, x);", 0),
+    ("spa_magnitude_includes_self",
+     "if (k2 == k) continue;\n                                if (Q[k2] < 0.0) sgn = -sgn;\n                                double a = fabs(Q[k2]);",
+     "if (Q[k2] < 0.0 && k2 != k) sgn = -sgn;\n                                double a = fabs(Q[k2]);", 0),
 ]
 
 
