@@ -111,4 +111,5 @@ def test_mutant_is_caught(tmp_path, name, old, new, occ):
                 pin(O)
             except (AssertionError, RuntimeError, ValueError, FloatingPointError):
                 failed.append(pin.__name__)
+                break  # one catching pin is enough
     assert failed, f"no pin caught mutant {name}"
