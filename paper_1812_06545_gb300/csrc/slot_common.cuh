@@ -7,7 +7,9 @@
 
 namespace ldpc {
 
-// phi in the two specialised forms of the streaming kernels (see flood_kernels.cu).
+// The approximate base-2 exponential and logarithm of the special-function units; phi
+// below is built from them in the two specialised forms of the streaming kernels (see
+// flood_kernels.cu).
 __device__ __forceinline__ float s_ex2(float x)
 {
     float y;
@@ -27,8 +29,8 @@ constexpr float kSLn2 = 0.6931471805599453f;
 // (LLR x log2 e) for a decoder that keeps APP, Q and R scaled (B2), where neither needs a
 // scaling multiply.
 
-// phi(x) in base-2 units for x = |Q| (already clamped), in base-2 units (B2) or natural
-// units.  ln((1 + t)/(1 - t)) is evaluated as lg2(1 + t) - lg2(1 - t): the two logarithms
+// phi(x), returned in base-2 units, of x = |Q| (already clamped) given in base-2 units (B2)
+// or in natural units.  ln((1 + t)/(1 - t)) is evaluated as lg2(1 + t) - lg2(1 - t): the two logarithms
 // are independent (a shorter dependency chain than a reciprocal followed by one logarithm)
 // and have opposite signs, so their difference does not cancel; for x above 3 (natural)
 // the series 2t + 2t^3/3 keeps the relative accuracy that the difference would lose.
