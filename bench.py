@@ -122,6 +122,9 @@ def parse_args():
     ap.add_argument("--no-paper-shape", action="store_true", help="skip the frame-length / stream sweep")
     ap.add_argument("--no-equal-fer", action="store_true", help="skip the equal-FER throughput comparison")
     ap.add_argument("--fer-frames", type=int, default=400000, help="frames per equal-FER point")
+    ap.add_argument("--details", default=os.environ.get("LDPC_BENCH_DETAILS") or
+                    os.path.join(tempfile.gettempdir(), "ldpc_bench_details.json"),
+                    help="file that receives every section of the run (the last stdout line is a summary)")
     return ap.parse_args()
 
 
@@ -333,6 +336,192 @@ def run_serving(ldpc, dev, window_s: float):
         ldpc.ldpc_session_destroy(sess)
 
 
+# ------------------------------------------------------------------ mixed codes (one launch)
+
+def run_mixed(ldpc, dev, rank, world, steps, warmup, max_over_ranks, barrier, n_total: int = 20000):
+    """20000 codewords, each of a code drawn uniformly from the 12-code family (Z in {27, 54,
+    81} x rate {1/2, 2/3, 3/4, 5/6}), every code at its FER ~1e-2 operating point, FP16
+    messages, max 20 iterations: one persistent ldpc_decode_multi launch per step.  Before
+    timing, ldpc_autotune picks each code's schedule on a sample of its own frames.  Timed
+    twice: eager calls, and replays of a CUDA graph that captured the call."""
+    import torch
+
+    from paper_1812_06545_gb300 import inputs as I
+
+    stream = torch.cuda.current_stream(dev)
+    mixed = I.mixed_batch(n_total, 40 + rank)
+    mp = ldpc.params_for("flood_f16", max_iter=20)
+    mreqs, mK, tuned = [], 0, {}
+    for name, c, L in mixed:
+        mb_, mZ = I.load_code(name)
+        mc = ldpc.Code(mb_, mZ)
+        x = torch.from_numpy(L).to(dev)
+        o = (torch.empty((len(L), mc.N), dtype=torch.uint8, device=dev),
+             torch.empty((len(L),), dtype=torch.int32, device=dev))
+        if len(L):
+            choice, tms = ldpc.ldpc_autotune(mc.handle, mp, x, ldpc.LDPC_LLR_F32, len(L), stream)
+            tuned[name] = {"choice": {1: "slots x1", 2: "slots x2", 3: "streaming"}.get(choice, str(choice)),
+                           "ms": [float(t) for t in tms]}
+        mreqs.append((mc, x, len(L), o[0], o[1], c))
+        mK += mc.K * len(L)
+    mws = torch.empty(ldpc.ldpc_multi_workspace_size(), dtype=torch.uint8, device=dev)
+    margs = [(q[0].handle, q[1], q[2], q[3], q[4], None) for q in mreqs]
+
+    def launch(st):
+        ldpc.ldpc_decode_multi(margs, mp, ldpc.LDPC_LLR_F32, mws, mws.numel(), st)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1))
+
+    for _ in range(max(warmup, 1)):
+        launch(stream)
+    eager_ms = timed(lambda: launch(stream))
+    eager_bits = [q[3].clone() for q in mreqs]
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        launch(side)
+    torch.cuda.synchronize()
+    for q in mreqs:
+        q[3].zero_()
+    for _ in range(max(warmup, 1)):
+        g.replay()
+    graph_ms = timed(g.replay)
+    same = all(torch.equal(q[3], b) for q, b in zip(mreqs, eager_bits))
+    n = sum(q[2] for q in mreqs)
+    errs = sum(int((q[3].cpu().numpy() != q[5]).any(axis=1).sum()) for q in mreqs)
+    per_code = {name: float((q[3].cpu().numpy() != q[5]).any(axis=1).mean()) if q[2] else None
+                for (name, _, _), q in zip(mixed, mreqs)}
+    return {"workload": f"mixed_12codes_b{n_total} (Z in {{27,54,81}} x rate {{1/2,2/3,3/4,5/6}}, each code at "
+                        "its FER~1e-2 operating point, FP16 messages, max 20 iterations)",
+            "api": "graph replay of one ldpc_decode_multi launch per step (eager calls timed beside it)",
+            "value": world * steps * mK / (graph_ms * 1e-3) / 1e9, "graph_info_gbps": world * steps * mK / (graph_ms * 1e-3) / 1e9,
+            "eager_info_gbps": world * steps * mK / (eager_ms * 1e-3) / 1e9, "ms_per_launch_graph": graph_ms / steps,
+            "ms_per_launch_eager": eager_ms / steps, "graph_equals_eager": bool(same), "codewords": n,
+            "fer": errs / n, "fer_per_code": per_code, "autotuned": tuned,
+            "frames": [(name, q[1], q[3], q[5]) for (name, _, _), q in zip(mixed, mreqs)]}
+
+
+def mixed_oracle_check(frames, per_code: int, budget_s: float):
+    """FER of the FP64 oracle and of the mixed launch on the first codewords of every code of
+    the mixed batch (the same frames), and the share of identical decisions."""
+    from oracle import oracle as O
+    from paper_1812_06545_gb300 import inputs as I
+
+    t0 = time.perf_counter()
+    go = oo = same = tot = 0
+    for name, x, bits, c in frames:
+        if time.perf_counter() - t0 > budget_s:
+            break
+        n = min(per_code, x.shape[0])
+        if n == 0:
+            continue
+        B, Z = I.load_code(name)
+        _, ob, _ = O.QCCode(B, Z).spa_flood(x[:n].cpu().numpy(), 20, True, fp16_msgs=True)
+        gb = bits[:n].cpu().numpy()
+        go += int((gb != c[:n]).any(axis=1).sum())
+        oo += int((ob != c[:n]).any(axis=1).sum())
+        same += int((gb == ob).all(axis=1).sum())
+        tot += n
+    return {"codewords": tot, "gpu_fer": go / max(tot, 1), "oracle_fer": oo / max(tot, 1),
+            "identical_decisions": same / max(tot, 1), "oracle": "FP64 flooding SPA with binary16 message storage"}
+
+
+# ------------------------------------------------------------------ the summary line
+
+SUMMARY_LIMIT = 2400     # bytes of the last stdout line
+
+
+def _sig(x, digits: int = 4):
+    """x with every float rounded to `digits` significant digits (non-finite -> None)."""
+    if isinstance(x, float):
+        if x != x or x in (float("inf"), float("-inf")):
+            return None
+        return float(f"{x:.{digits}g}")
+    if isinstance(x, dict):
+        return {k: _sig(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_sig(v, digits) for v in x]
+    return x
+
+
+def summary_line(line: dict, details_path: str) -> dict:
+    """The run's last stdout line: the required keys and the headline figure of every section,
+    rounded, within SUMMARY_LIMIT bytes.  The optional sections join in priority order (serving,
+    the equal-FER ratios, the forms), each only if the line still fits; every section in full
+    is in the details file."""
+    out = {k: line[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                                "higher_is_better", "scaling", "vs_baseline", "dtype", "data")}
+    cfg = line["config"]
+    out["config"] = {"workload": cfg["workload"], "code": cfg["code"], "N": cfg["N"], "K": cfg["K"],
+                     "batch": cfg["batch"], "ebn0_db": "1.0-2.5 step 0.25", "max_iter": cfg["max_iter"],
+                     "early_exit": True, "parallelism": cfg["parallelism"], "l2": "inputs larger than L2"}
+    rf = line["roofline"]
+    out["roofline"] = {"bound": rf["bound"], "kernel": "k_flood_slots", "achieved": rf["achieved"],
+                       "peak": rf["peak"], "unit": rf["unit"], "frac": rf["frac"], "traffic": rf["traffic"],
+                       "peak_source": "SFU rates measured live: 1/(2/ex2+4/lg2) edge updates/s"}
+    out["latency_ms"] = {"p50": line["latency_ms"]["p50"], "p99": line["latency_ms"]["p99"]}
+    e2e = line["e2e"]
+    out["e2e"] = {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "streams")}
+    for k in ("gpu_launches", "avg_iterations", "coded_bit_iterations_per_s"):
+        out[k] = line[k]
+    clk = line.get("clocks") or {}
+    out["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons") if k in clk} or clk
+    if "cpu_baseline" in line:
+        cb = line["cpu_baseline"]
+        out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        d = cb.get("fer_delta_vs_oracle", {})
+        out["cpu_baseline"]["fer_delta_max"] = {f: max(abs(v["delta"]) for v in r["per_ebn0"].values())
+                                                for f, r in d.items()}
+        if "mixed_f16" in cb:
+            out["cpu_baseline"]["mixed_fer_delta"] = cb["mixed_f16"]["gpu_fer"] - cb["mixed_f16"]["oracle_fer"]
+    opt = []
+    sv = line.get("serving")
+    if sv:
+        opt.append(("serving", {"capacity_gbps": sv["capacity"]["info_gbps"], **sv["at_saturation"],
+                                "p99_ms_quarter_load": sv["sweep"][0]["p99_ms"], "valid": sv["valid"]}))
+    ef = line.get("equal_fer")
+    if ef:
+        eq = {}
+        for c in ef["codes"]:
+            eq[c["code"]] = {"ebn0_star_db": c["ebn0_star_db"], "plain_f32_gbps": c["reference"]["info_gbps"]}
+            for r in c["forms"]:
+                eq[c["code"]][r["form"]] = [r["ratio_vs_plain_f32"], r.get("ratio_vs_flood_f32"),
+                                            r["fer_within_10pct"]]
+        opt.append(("equal_fer", eq))
+    f = line.get("forms")
+    if f:
+        gb = {k: f[k]["value"] for k in ("flood_f16", "layered_f32", "layered_f16", "stream_f32", "stream_f16",
+                                          "plain_f32", "layered_i8") if k in f}
+        if "mixed_f16" in f:
+            gb["mixed_f16_graph"] = f["mixed_f16"]["graph_info_gbps"]
+            gb["mixed_f16_eager"] = f["mixed_f16"]["eager_info_gbps"]
+        if "large_code" in f:
+            gb["n26112_f16"] = f["large_code"]["cluster_f16"]["value"]
+        extra = {"stream_f32_hbm_frac": f.get("stream_f32", {}).get("roofline", {}).get("frac"),
+                 "layered_i8_gedge_s": f.get("layered_i8", {}).get("edge_updates_per_s", 0) / 1e9}
+        opt.append(("forms_gbps", gb))
+        opt.append(("forms_extra", extra))
+    out["details"] = details_path
+    out = _sig(out)
+    opt = [(k, _sig(v)) for k, v in opt]
+    for k, v in opt:                 # in priority order; a section that would not fit is left out
+        trial = dict(out, **{k: v})
+        if len(json.dumps(trial)) <= SUMMARY_LIMIT:
+            out = trial
+    return out
+
+
 # ------------------------------------------------------------------ reference arm (the oracle)
 
 # rate-1/2 codes at the frame lengths of the paper's throughput figures (Sec. IV)
@@ -344,57 +533,92 @@ def run_paper_shape(ldpc, dev, reps: int = 3):
     """Throughput over frame length for a fixed number of layered iterations (5 and 10, no
     early exit), the shape of the paper's Sec. IV measurements: end to end through the host
     API (pinned LLRs in, decisions out, copies included) with W = 1 and W = 3 streams, and the
-    device-resident decode alone.  2^24 coded bits per run, 2.0 dB."""
+    device-resident decode alone.  2^24 coded bits per run at 2.0 dB, each row with its FER.
+    At 2.0 dB the int8 min-sum fails most frames of the long codes, so every code also gets an
+    int8 row at its own operating point: the lowest Eb/N0 on a 0.25 dB grid from 2.0 dB at
+    which 10 iterations give FER <= 1e-2 (noise drawn on the device, seeded)."""
     import torch
 
     from paper_1812_06545_gb300 import inputs as I
 
     out = []
     stream = torch.cuda.current_stream(dev)
+
+    def device_llr(c_dev, rate, eb, seed):
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        s2 = 1.0 / (2.0 * rate * 10.0 ** (eb / 10.0))
+        y = (1.0 - 2.0 * c_dev.float()) + (s2 ** 0.5) * torch.randn(c_dev.shape, generator=g, device=dev)
+        return (2.0 / s2) * y
+
     for name in PAPER_SHAPE_CODES:
         B, Z = I.load_code(name)
         code = ldpc.Code(B, Z)
         n = (1 << 24) // code.N
+        rate = code.K / code.N
         _, _, c, L = I.make_frames(name, n, 2.0, 71, 72)
         Lh = torch.from_numpy(L).pin_memory()
         bh = torch.empty((n, code.N), dtype=torch.uint8).pin_memory()
         ih = torch.empty((n,), dtype=torch.int32).pin_memory()
         Ld = Lh.to(dev)
+        c_dev = torch.from_numpy(c).to(dev)
         bd = torch.empty((n, code.N), dtype=torch.uint8, device=dev)
         idv = torch.empty((n,), dtype=torch.int32, device=dev)
         chunk = (n + 11) // 12
-        for form in ("layered_f32", "layered_i8"):
-            for T in (5, 10):
-                kw = {"llr_scale": I.llr_scale_for(code.K / code.N, 2.0)} if form == "layered_i8" else {}
-                p = ldpc.params_for(form, max_iter=T, early_exit=0, **kw)
-                wsb = ldpc.ldpc_workspace_size(code.handle, p, n)
-                ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+
+        def device_rate(p, x):
+            wsb = ldpc.ldpc_workspace_size(code.handle, p, n)
+            ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=dev)
+            times = []
+            for r in range(reps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ldpc.ldpc_decode_batch(code.handle, p, x, ldpc.LDPC_LLR_F32, n, bd, idv, None, ws, wsb, stream)
+                e1.record(stream)
+                e1.synchronize()
+                if r:
+                    times.append(e0.elapsed_time(e1) * 1e-3)
+            return n * code.K / float(np.median(times)) / 1e9, float((bd != c_dev).any(dim=1).float().mean())
+
+        def host_rates(p, Lhost, row):
+            for W in (1, 3):
                 times = []
                 for r in range(reps + 1):
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    ldpc.ldpc_decode_batch(code.handle, p, Ld, ldpc.LDPC_LLR_F32, n, bd, idv, None, ws, wsb, stream)
-                    e1.record(stream)
-                    e1.synchronize()
+                    t0 = time.perf_counter()
+                    ldpc.ldpc_decode_host(code.handle, p, Lhost, n, bh, ih, n_streams=W, chunk_cw=chunk)
                     if r:
-                        times.append(e0.elapsed_time(e1) * 1e-3)
+                        times.append(time.perf_counter() - t0)
+                row[f"e2e_info_gbps_w{W}"] = n * code.K / float(np.median(times)) / 1e9
+            row["fer"] = float((bh.numpy() != c).any(axis=1).mean())
+
+        for form in ("layered_f32", "layered_i8"):
+            for T in (5, 10):
+                kw = {"llr_scale": I.llr_scale_for(rate, 2.0)} if form == "layered_i8" else {}
+                p = ldpc.params_for(form, max_iter=T, early_exit=0, **kw)
+                gbps, _ = device_rate(p, Ld)
                 row = {"code": name, "N": code.N, "K": code.K, "codewords": n, "form": form, "iterations": T,
-                       "device_info_gbps": n * code.K / float(np.median(times)) / 1e9}
-                for W in (1, 3):
-                    times = []
-                    for r in range(reps + 1):
-                        t0 = time.perf_counter()
-                        ldpc.ldpc_decode_host(code.handle, p, Lh, n, bh, ih, n_streams=W, chunk_cw=chunk)
-                        if r:
-                            times.append(time.perf_counter() - t0)
-                    row[f"e2e_info_gbps_w{W}"] = n * code.K / float(np.median(times)) / 1e9
-                row["fer"] = float((bh.numpy() != c).any(axis=1).mean())
+                       "ebn0_db": 2.0, "device_info_gbps": gbps}
+                host_rates(p, Lh, row)
                 out.append(row)
+        # int8 at its own operating point (FER <= 1e-2 at 10 iterations)
+        eb = 2.0
+        while eb <= 6.0:
+            p = ldpc.params_for("layered_i8", max_iter=10, early_exit=0, llr_scale=I.llr_scale_for(rate, eb))
+            x = device_llr(c_dev, rate, eb, 7300 + int(eb * 100))
+            gbps, fer = device_rate(p, x)
+            if fer <= 1e-2:
+                row = {"code": name, "N": code.N, "K": code.K, "codewords": n, "form": "layered_i8",
+                       "iterations": 10, "ebn0_db": eb, "operating_point": "FER <= 1e-2", "device_info_gbps": gbps}
+                host_rates(p, x.cpu().pin_memory(), row)
+                out.append(row)
+                break
+            eb += 0.25
         ldpc.ldpc_release_host_buffers()
         del code
     return {"what": "info Gbit/s over frame length, fixed layered iterations (no early exit), 2^24 coded bits per "
-                    "run at 2.0 dB; e2e through ldpc_decode_host with W streams (12 chunks), device = decode of "
-                    "HBM-resident LLRs", "rows": out}
+                    "run at 2.0 dB, plus an int8 row per code at its FER <= 1e-2 operating point; e2e through "
+                    "ldpc_decode_host with W streams (12 chunks), device = decode of HBM-resident LLRs; fer "
+                    "of every row beside its throughput", "rows": out}
 
 
 def run_equal_fer(ldpc, dev, n_frames: int = 400000, chunk: int = 50000):
@@ -496,12 +720,16 @@ def run_equal_fer(ldpc, dev, n_frames: int = 400000, chunk: int = 50000):
                         break
                     prev = (eb2, r2["fer"])
             rows.append(best)
+        f32 = [r for r in rows if r["form"] == "flood_f32"]
+        for r in rows:
+            r["ratio_vs_flood_f32"] = r["info_gbps"] / f32[0]["info_gbps"] if f32 else None
         out.append({"code": name, "N": code.N, "K": code.K, "ebn0_star_db": float(e_star),
                     "sweep_fp32_flooding": [{"ebn0_db": e, "fer": f} for e, f in pts], "reference": ref,
                     "forms": rows})
         del code
     return {"what": "info Gbit/s at equal FER: E* where FP32 flooding (max 20, early exit) has FER 1e-3; each "
-                    "form at the smallest max_iter whose FER is within 10 % of the plain FP32 comparator's at E*",
+                    "form at the smallest max_iter whose FER is within 10 % of the plain FP32 comparator's at E*; ratios against "
+                    "the plain comparator and against the optimised FP32 flooding decoder",
             "codes": out}
 
 
@@ -818,37 +1046,11 @@ def main():
         lms = max_over_ranks(e0.elapsed_time(e1))
         lv = world * args.steps * lw.batch * lcode.K / (lms * 1e-3) / 1e9
         lit_np = lit.cpu().numpy()
-        # mixed codes in one persistent launch: 20000 codewords over 12 codes (FP16 messages)
-
-        mixed = I.mixed_batch(20000, 40 + rank)
-        mreqs, mouts, mK = [], [], 0
-        for name, c, L in mixed:
-            mb_, mZ = I.load_code(name)
-            mc = ldpc.Code(mb_, mZ)
-            x = torch.from_numpy(L).to(dev)
-            o = (torch.empty((len(L), mc.N), dtype=torch.uint8, device=dev),
-                 torch.empty((len(L),), dtype=torch.int32, device=dev))
-            mreqs.append((mc, x, len(L), o[0], o[1], None, c))
-            mK += mc.K * len(L)
-        mp = ldpc.params_for("flood_f16", max_iter=20)
-        mws = torch.empty(ldpc.ldpc_multi_workspace_size(), dtype=torch.uint8, device=dev)
-        margs = [(q[0].handle, q[1], q[2], q[3], q[4], None) for q in mreqs]
-        for _ in range(args.warmup):
-            ldpc.ldpc_decode_multi(margs, mp, ldpc.LDPC_LLR_F32, mws, mws.numel(), stream)
-        torch.cuda.synchronize()
-        barrier()
-        e0.record(stream)
-        for _ in range(args.steps):
-            ldpc.ldpc_decode_multi(margs, mp, ldpc.LDPC_LLR_F32, mws, mws.numel(), stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        mms = max_over_ranks(e0.elapsed_time(e1))
-        merr = sum(int((q[3].cpu().numpy() != q[6]).any(axis=1).sum()) for q in mreqs)
-        forms["mixed_f16"] = {"workload": "mixed_12codes_b20000 (Z in {27,54,81} x rate {1/2,2/3,3/4,5/6}, "
-                                          "each code at its FER~1e-2 operating point)",
-                              "value": world * args.steps * mK / (mms * 1e-3) / 1e9, "ms_per_launch": mms / args.steps,
-                              "codewords": sum(q[2] for q in mreqs), "fer": merr / sum(q[2] for q in mreqs),
-                              "api": "ldpc_decode_multi (one launch per step)"}
+        # mixed codes in one persistent launch: 20000 codewords over 12 codes (FP16 messages),
+        # schedules autotuned per code, the launch captured in a CUDA graph and replayed
+        mixed = run_mixed(ldpc, dev, rank, world, args.steps, args.warmup, max_over_ranks, barrier)
+        mixed_frames = mixed.pop("frames")
+        forms["mixed_f16"] = mixed
         forms["layered_i8"] = {"workload": LAYERED_WORKLOAD, "code": lw.code, "value": lv,
                                "ms_per_decode": lms / args.steps, "avg_iterations": float(lit_np.mean()),
                                "fer": {f"{lw.ebn0_db[0]:.2f}": float((lbits.cpu().numpy() != lframes[0][1])
@@ -915,7 +1117,14 @@ def main():
             deltas[form] = {"per_ebn0": per, "identical_decisions": same / tot}
         line["cpu_baseline"]["fer_delta_vs_oracle"] = deltas
     if rank == 0:
-        print(json.dumps(line))
+        if not args.no_forms and not args.no_cpu_baseline and "cpu_baseline" in line:
+            line["cpu_baseline"]["mixed_f16"] = mixed_oracle_check(mixed_frames, 64, 6.0)
+        try:
+            with open(args.details, "w") as f:
+                json.dump(line, f, indent=1)
+        except OSError as ex:
+            print(f"bench: could not write {args.details}: {ex}", file=sys.stderr)
+        print(json.dumps(summary_line(line, args.details)))
     if dist:
         dist.barrier()
         dist.destroy_process_group()

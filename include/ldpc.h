@@ -320,7 +320,11 @@ void ldpc_launch_count_reset(void);
  *     or LDPC_IMPL_PLAIN the scratch grows in tiles of 128 codewords (up to 896 codewords
  *     of the N = 1944 rate-1/2 code with FP32 messages).
  *   - The first call on each device looks up the array's device address (with that device
- *     current) and keeps it; make that first call before any stream capture begins.
+ *     current) and keeps it; make that first call before any stream capture begins.  Under
+ *     CUDA's lazy module loading (the default) that lookup is also what loads the part of
+ *     the library holding the array, so the first call is the one that reserves the array's
+ *     device memory (a failure there is reported as LDPC_ECUDA).  Make it at start-up, with
+ *     a small batch; later calls reserve nothing.
  *   - All calls share the one array and it keeps whatever the last call left in it (the
  *     kernels initialise every part they read).  Calls whose work overlaps on the GPU -
  *     on different streams, or from different host threads without ordering - corrupt each

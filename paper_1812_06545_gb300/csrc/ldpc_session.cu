@@ -415,14 +415,19 @@ ldpc_status ldpc_session_wait(ldpc_session *s, uint64_t id, double timeout_s, do
     if (it == s->reqs.end()) return sfail(LDPC_EINVAL, "unknown or already collected request id");
     const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
                                              std::chrono::duration<double>(timeout_s < 0 ? 0 : timeout_s));
-    while (!terminal(s->reqs[id].state)) {
-        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !terminal(s->reqs[id].state))
+    // the record is looked up again after every wait: another thread may have collected it
+    // (poll or wait) meanwhile, and operator[] would then insert a fresh queued record
+    while (!terminal(it->second.state)) {
+        const bool timed_out = s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout;
+        it = s->reqs.find(id);
+        if (it == s->reqs.end()) return sfail(LDPC_EINVAL, "request collected by another caller while waiting");
+        if (timed_out && !terminal(it->second.state))
             return sfail(LDPC_ETIMEDOUT, "request not finished within the timeout");
     }
-    SessReq &r = s->reqs[id];
+    SessReq &r = it->second;
     if (latency_s) *latency_s = std::chrono::duration<double>(r.t_done - r.t_submit).count();
     const ldpc_status st = r.status;
-    s->reqs.erase(id);
+    s->reqs.erase(it);
     return st;
 }
 

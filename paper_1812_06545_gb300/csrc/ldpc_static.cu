@@ -9,8 +9,10 @@
 namespace {
 
 // The scratch of every call: LDPC_STATIC_SCRATCH_BYTES of device memory, reserved on each
-// GPU that loads the library for the life of the process.  In host code this name is only
-// a host-side stand-in; the device address comes from cudaGetSymbolAddress below.
+// GPU that loads this part of the library, for the life of the process (with lazy module
+// loading that happens at the address lookup of the first call on the device).  In host
+// code this name is only a host-side stand-in; the device address comes from
+// cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_scratch[LDPC_STATIC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 # codes covering the three kernel shapes: check degree <= 8 (4 codewords per lane),
 # <= 16 (2 per lane) and <= 32 (1 per lane); batch sizes leave a ragged last tile.
 CASES = [("qc12x24_z81_s2", 260, 1.5), ("qc12x24_z27_s1", 300, 2.0), ("qc8x24_z54_s45", 140, 2.5),
-         ("qc4x24_z27_s43", 130, 3.5)]
+         ("qc4x24_z27_s43", 130, 3.5), ("qc10x20_z200_s10", 170, 2.0)]
 
 _gcodes = {}
 
@@ -229,3 +229,51 @@ def test_argument_errors(cuda_dev):
     assert ei.value.status == ldpc.LDPC_ENOMEM
     ldpc.ldpc_decode_batch(code.handle, p, x, 0, 4, b, i, None, ws, need)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("form", ["flood_f32", "flood_f16"])
+def test_multistream_host_path_against_the_oracle(cuda_dev, form):
+    # Sec. III-C: W = 3 streams, each chunk copied in, decoded and copied out on its own
+    # stream.  (1) Three iterations without early exit: every decision at a bit whose oracle
+    # posterior lies outside the tolerance band around 0 equals the oracle's.  (2) The
+    # full-size workload (8192 codewords at 1.5 and 2.0 dB, early exit, max 20) through the
+    # host path: decisions and iteration counts against the oracle, FER inside its 95 %
+    # interval, as for the device path.
+    name = "qc12x24_z81_s2"
+    code = gpu_code(name)
+    oc = oracle_code(name)
+    f16 = form.endswith("f16")
+
+    def host_decode(L, p):
+        n = L.shape[0]
+        Lh = torch.from_numpy(L).pin_memory()
+        bh = torch.empty((n, code.N), dtype=torch.uint8).pin_memory()
+        ih = torch.empty((n,), dtype=torch.int32).pin_memory()
+        ldpc.ldpc_decode_host(code.handle, p, Lh, n, bh, ih, n_streams=3, chunk_cw=700)
+        return bh.numpy().copy(), ih.numpy().copy()
+
+    _, _, c, L = I.make_frames(name, 2100, 1.75, 111, 112)
+    bits, iters = host_decode(L, ldpc.params_for(form, max_iter=3, early_exit=0))
+    assert (iters == 3).all()
+    ref, rbits, _, R = oc.spa_flood(L, 3, early_exit=False, fp16_msgs=f16, return_messages=True)
+    band = FP32_TOL * np.maximum(1.0, np.abs(ref)) + (4 * 2.0 ** -11 * oc.incoming_message_sum(R) if f16 else 0)
+    clear = np.abs(ref) > band
+    assert np.array_equal(bits[clear], rbits[clear])
+    mism = tot = 0
+    for eb, seed in ((1.5, 23), (2.0, 25)):
+        _, _, c, L = I.make_frames(name, 8192, eb, 20, seed)
+        bits, iters = host_decode(L, ldpc.params_for(form, max_iter=20, early_exit=1))
+        _, rbits, riters = oc.spa_flood(L, 20, early_exit=True, fp16_msgs=f16)
+        same = (bits == rbits).all(axis=1)
+        mism += int((~same).sum())
+        tot += len(same)
+        fer_g, fer_o = int((bits != c).any(axis=1).sum()), int((rbits != c).any(axis=1).sum())
+        lo, hi = clopper_pearson(fer_o, len(c))
+        assert lo <= fer_g / len(c) <= hi, (form, eb, fer_g, fer_o)
+        conv = riters < 20
+        assert (iters[conv & same] == riters[conv & same]).mean() >= 0.999
+        if f16:
+            both = conv & (iters < 20)
+            assert same[both].mean() >= 0.9999, (eb, int((~same[both]).sum()))
+    if not f16:
+        assert mism <= 1e-4 * tot, (form, mism, tot)

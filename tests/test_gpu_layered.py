@@ -89,6 +89,18 @@ def test_large_code_z384(cuda_dev, form):
     assert_exact(got, oracle_code(name).nms_layered(q, 10, early_exit=True))
 
 
+@pytest.mark.parametrize("form", ["layered_i8", "layered_i8_group"])
+@pytest.mark.parametrize("name,n,eb", [("qc10x20_z200_s10", 400, 2.75), ("qc20x40_z200_s11", 300, 2.5)])
+def test_paper_frame_lengths_z200(cuda_dev, form, name, n, eb):
+    # the paper's frame lengths N = 4000 and 8000 (Sec. IV) with Z = 200 (lanes not a multiple
+    # of 32, seven warps per slot), fp32 LLRs quantised in the kernel, 10 iterations
+    _, _, c, L = I.make_frames(name, n, eb, 52, 53)
+    scale = I.llr_scale_for(0.5, eb)
+    got = run(gpu_code(name), L, cuda_dev, form, max_iter=10, llr_scale=scale)
+    q = O.quantize(L, scale, 31)
+    assert_exact(got, oracle_code(name).nms_layered(q, 10, early_exit=True))
+
+
 def test_eq1_code_z1(cuda_dev):
     H = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "eq1_H.txt"))
     base = np.where(H == 1, 0, -1).astype(np.int32)

@@ -16,7 +16,9 @@ pytestmark = pytest.mark.gpu
 # check degrees <= 8 (exact bodies, messages held), <= 16 and <= 32 (bucketed bodies,
 # register-lean form); batch sizes are not multiples of the slots of one CTA.
 CASES = [("qc12x24_z81_s2", 260, 1.5), ("qc12x24_z27_s1", 300, 2.0), ("qc8x24_z54_s45", 140, 2.5),
-         ("qc4x24_z27_s43", 130, 3.5), ("qc4x24_z81_s3", 97, 3.5)]
+         ("qc4x24_z27_s43", 130, 3.5), ("qc4x24_z81_s3", 97, 3.5),
+         # the paper's frame lengths N = 4000 and 8000 (Sec. IV), Z = 200
+         ("qc10x20_z200_s10", 170, 2.0), ("qc20x40_z200_s11", 160, 2.0)]
 
 _gcodes = {}
 

@@ -4,8 +4,10 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as O
 from paper_1812_06545_gb300 import inputs as I
 from paper_1812_06545_gb300 import ldpc
+from tests.gpu_helpers import FP32_TOL, oracle_code, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -107,3 +109,47 @@ def test_mixed_launch_with_a_cluster_sized_code(cuda_dev):
     torch.cuda.synchronize()
     for o, (rb, ri, _) in zip(outs, refs):
         assert torch.equal(o[0], rb) and torch.equal(o[1], ri)
+
+
+@pytest.mark.parametrize("form", ["flood_f32", "flood_f16", "layered_f32", "layered_f16", "layered_i8"])
+def test_mixed_launch_against_the_oracle(cuda_dev, form):
+    # One ldpc_decode_multi call over all 12 family codes (request sizes 1..512, ragged)
+    # against the oracle, code by code: the sum-product forms after 3 iterations without early
+    # exit, element by element within the FP32 tolerance (plus the binary16 rounding terms of
+    # the FP16 forms: 4 half-ulps of every incoming message for flooding, 8 for layered); the
+    # int8 min-sum bit-exact (posterior, decisions, iteration counts) at max 10 with early exit
+    i8 = form == "layered_i8"
+    layered = form.startswith("layered")
+    p = ldpc.params_for(form, max_iter=10 if i8 else 3, early_exit=1 if i8 else 0)
+    sizes = [1, 37, 300, 129, 64, 512, 7, 250, 3, 90, 200, 33]
+    reqs, outs, Ls = [], [], []
+    for i, name in enumerate(FAMILY):
+        code = gpu_code(name)
+        n = sizes[i]
+        _, _, c, L = frames(name, n, 700 + i)
+        x = torch.from_numpy(L).to(cuda_dev)
+        o = outputs(code, n, cuda_dev)
+        reqs.append((code.handle, x, n, o[0], o[1], o[2]))
+        outs.append(o)
+        Ls.append(L)
+    ldpc.ldpc_decode_multi(reqs, p)
+    torch.cuda.synchronize()
+    for name, L, o in zip(FAMILY, Ls, outs):
+        oc = oracle_code(name)
+        app, bits, iters = (t.cpu().numpy() for t in (o[2], o[0], o[1]))
+        if i8:
+            q = O.quantize(L, 2.0, 31)
+            ra, rb, ri = oc.nms_layered(q, 10, early_exit=True)
+            assert np.array_equal(iters, ri) and np.array_equal(app.astype(np.int32), ra), name
+            assert np.array_equal(bits, rb), name
+            continue
+        assert (iters == 3).all()
+        orc = oc.spa_layered if layered else oc.spa_flood
+        if form.endswith("f16"):
+            ref, _, _, R = orc(L, 3, early_exit=False, fp16_msgs=True, return_messages=True)
+            tol = FP32_TOL * np.maximum(1.0, np.abs(ref)) + (8 if layered else 4) * 2.0 ** -11 * \
+                oc.incoming_message_sum(R)
+            assert (np.abs(app - ref) <= tol).all(), (form, name)
+        else:
+            ref, _, _ = orc(L, 3, early_exit=False)
+            assert rel_err(app, ref).max() <= FP32_TOL, (form, name, rel_err(app, ref).max())

@@ -5,8 +5,10 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as O
 from paper_1812_06545_gb300 import inputs as I
 from paper_1812_06545_gb300 import ldpc
+from tests.gpu_helpers import clopper_pearson, oracle_code
 
 pytestmark = pytest.mark.gpu
 
@@ -73,8 +75,44 @@ def test_same_alone_and_in_the_mix(cuda_dev):
             assert np.array_equal(j.bits.numpy(), b) and np.array_equal(j.iters.numpy(), i), (j.name, j.form)
         stats = ldpc.ldpc_session_stats_get(s)
         assert stats.completed == len(ids) + 1 and stats.failed == 0 and stats.launches < len(ids) + 1
+        check_against_oracle(jobs + [target])
     finally:
         ldpc.ldpc_session_destroy(s)
+
+
+def check_against_oracle(jobs):
+    """Every served request against the oracle: the int8 min-sum bit-exact (decisions and
+    iteration counts); the sum-product forms with identical decisions on >= 99.99 % of the
+    codewords (FP16: wherever both decoders converged), iteration counts of converged
+    codewords, and a frame error rate inside the oracle's 95 % interval over all requests."""
+    stats = {"flood_f32": [0, 0, 0, 0], "flood_f16": [0, 0, 0, 0]}   # mismatches, codewords, gpu/oracle errors
+    for j in jobs:
+        oc = oracle_code(j.name)
+        L = j.llr.numpy()
+        bits, iters = j.bits.numpy(), j.iters.numpy()
+        if j.form == "layered_i8":
+            _, rb, ri = oc.nms_layered(O.quantize(L, 2.0, 31), 10, early_exit=True)
+            assert np.array_equal(bits, rb) and np.array_equal(iters, ri), j.name
+            continue
+        f16 = j.form == "flood_f16"
+        _, rb, ri = oc.spa_flood(L, 20, early_exit=True, fp16_msgs=f16)
+        same = (bits == rb).all(axis=1)
+        conv = ri < 20
+        assert (iters[conv & same] == ri[conv & same]).mean() >= 0.999 if (conv & same).any() else True
+        if f16:
+            same = same[conv & (iters < 20)]
+        st = stats[j.form]
+        st[0] += int((~same).sum())
+        st[1] += len(same)
+        st[2] += int((bits != j.c).any(axis=1).sum())
+        st[3] += int((rb != j.c).any(axis=1).sum())
+    for form, (mism, tot, eg, eo) in stats.items():
+        if tot == 0:
+            continue
+        assert mism <= 1e-4 * tot, (form, mism, tot)
+        n = sum(j.n for j in jobs if j.form == form)
+        lo, hi = clopper_pearson(eo, n)
+        assert lo <= eg / n <= hi, (form, eg, eo, n)
 
 
 def test_admission_by_memory_budget(cuda_dev):
@@ -143,5 +181,37 @@ def test_large_code_request_decodes_alone(cuda_dev):
         assert ldpc.ldpc_session_wait(s, rid, 60.0)[0] == ldpc.LDPC_OK
         b, i = j.reference(cuda_dev)
         assert np.array_equal(j.bits.numpy(), b) and np.array_equal(j.iters.numpy(), i)
+    finally:
+        ldpc.ldpc_session_destroy(s)
+
+
+def test_two_waiters_on_one_request(cuda_dev):
+    # two host threads wait for the same request: the first to wake collects it, the other
+    # learns at once that it was collected (LDPC_EINVAL) instead of waiting out its timeout
+    import threading
+    import time
+
+    s = session(start_paused=1)
+    try:
+        j = Job("qc12x24_z27_s40", "flood_f32", 40, 95)
+        rid = j.submit(s)
+        res = []
+
+        def waiter():
+            t0 = time.perf_counter()
+            st, _ = ldpc.ldpc_session_wait(s, rid, 30.0)
+            res.append((st, time.perf_counter() - t0))
+
+        ts = [threading.Thread(target=waiter) for _ in range(2)]
+        for t in ts:
+            t.start()
+        time.sleep(0.3)
+        ldpc.ldpc_session_pause(s, False)
+        for t in ts:
+            t.join(60.0)
+        assert sorted(r[0] for r in res) == [ldpc.LDPC_EINVAL, ldpc.LDPC_OK], res
+        assert max(r[1] for r in res) < 20.0, res
+        b, i = j.reference(cuda_dev)
+        assert np.array_equal(j.bits.numpy(), b)
     finally:
         ldpc.ldpc_session_destroy(s)
