@@ -137,8 +137,12 @@ ldpc_status ldpc_decode_batch(const ldpc_code *code, const ldpc_decode_params *p
 /* Choose, by timing, the schedule ldpc_decode_batch / ldpc_decode_multi use for this code
  * and form with impl AUTO, and remember it in the code object.
  *   Flooding forms: the on-chip slot decoder with one or two codewords per thread (where
- *   the code fits), or the HBM-streaming kernels.  Layered min-sum: persistent slots or the
- *   fixed group per CTA.  The layered sum-product has one schedule: LDPC_ENOTSUP.
+ *   the code fits), or the HBM-streaming kernels.  Layered min-sum: persistent slots with one
+ *   codeword per thread (32-bit integer arithmetic) or two per thread (packed half-precision
+ *   integer arithmetic, offered when it is exact for the params: every message magnitude
+ *   (alpha_num * msg_sat) >> alpha_shift <= 127 and 2 * alpha_num * msg_sat +
+ *   2^alpha_shift <= 2047), or the fixed group per CTA.  Untuned, AUTO takes two per thread
+ *   where offered.  The layered sum-product has one schedule: LDPC_ENOTSUP.
  *   llr_dev / llr_type / n_cw  a representative device sample of the workload (>= 1 codeword).
  *   choice     receives the pick: 1 slots (1 codeword per thread), 2 slots (2 per thread),
  *              3 streaming / fixed group (may be NULL).

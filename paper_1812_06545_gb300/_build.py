@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libldpc_gb300.so")
-SOURCES = ["ldpc_api.cu", "flood_kernels.cu", "flood_slots.cu", "flood_cluster.cu", "layered_kernels.cu", "layered_spa.cu", "ldpc_static.cu",
+SOURCES = ["ldpc_api.cu", "flood_kernels.cu", "flood_slots.cu", "flood_cluster.cu", "layered_kernels.cu", "layered_pairs.cu", "layered_spa.cu", "ldpc_static.cu",
            "ldpc_session.cu", "ldpc_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

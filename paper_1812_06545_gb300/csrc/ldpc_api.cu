@@ -339,6 +339,25 @@ static bool use_layered_slots(const ldpc_code *c, const ldpc_decode_params *p)
            ldpc::layered_slots_per_cta(c->host) > 0 && c->tuned_layered != SCHED_STREAMING;
 }
 
+// The layered min-sum's persistent slots carry two codewords per thread in packed half
+// precision where that is exact for the parameters, unless tuning picked one per thread.
+#ifndef LDPC_LAYERED_PAIRS
+#define LDPC_LAYERED_PAIRS 1  // 0: the min-sum slots always carry one codeword per thread
+#endif
+static bool use_layered_pairs(const ldpc_code *c, const ldpc_decode_params *p)
+{
+    return LDPC_LAYERED_PAIRS && c->tuned_layered != SCHED_SLOTS_V1 && ldpc::layered_pairs_exact(*p) &&
+           ldpc::layered_pairs_per_cta(c->host) > 0;
+}
+static cudaError_t layered_slots_any(const ldpc_code *c, const ldpc_decode_params &p, const void *llr, int llr_type,
+                                     int64_t n_cw, uint8_t *bits, int32_t *iters, float *app, void *ws,
+                                     cudaStream_t s)
+{
+    return use_layered_pairs(c, &p)
+               ? ldpc::layered_pairs_decode(c->host, c->dev, p, llr, llr_type, n_cw, bits, iters, app, ws, s)
+               : ldpc::layered_slots_decode(c->host, c->dev, p, llr, llr_type, n_cw, bits, iters, app, ws, s);
+}
+
 // The layered sum-product always runs as persistent slots (check_params admits only codes
 // whose slot fits a CTA).
 static bool use_layered_spa(const ldpc_decode_params *p)
@@ -400,7 +419,7 @@ ldpc_status ldpc_decode_batch(const ldpc_code *c, const ldpc_decode_params *p, c
         e = ldpc::layered_spa_decode(c->host, c->dev, *p, static_cast<const float *>(llr), n_cw, bits, iters, app, ws,
                                      s);
     } else if (use_layered_slots(c, p)) {
-        e = ldpc::layered_slots_decode(c->host, c->dev, *p, llr, llr_type, n_cw, bits, iters, app, ws, s);
+        e = layered_slots_any(c, *p, llr, llr_type, n_cw, bits, iters, app, ws, s);
     } else if (use_slots(c, p)) {
         const ldpc::HostReq rq = {c, llr, n_cw, bits, iters, app};
         e = ldpc::flood_multi_decode(&rq, 1, *p, ws, s);
@@ -488,8 +507,8 @@ ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldp
                         ? ldpc::layered_spa_decode(hr[i].code->host, hr[i].code->dev, *p,
                                                    static_cast<const float *>(hr[i].llr), hr[i].n_cw, hr[i].bits,
                                                    hr[i].iters, hr[i].app, ws, s)
-                        : ldpc::layered_slots_decode(hr[i].code->host, hr[i].code->dev, *p, hr[i].llr, llr_type,
-                                                     hr[i].n_cw, hr[i].bits, hr[i].iters, hr[i].app, ws, s);
+                        : layered_slots_any(hr[i].code, *p, hr[i].llr, llr_type, hr[i].n_cw, hr[i].bits,
+                                            hr[i].iters, hr[i].app, ws, s);
     }
     if (own) {
         cudaError_t e2 = cudaFreeAsync(ws, s);
@@ -518,6 +537,7 @@ ldpc_status ldpc_autotune(ldpc_code *c, const ldpc_decode_params *p, const void 
         }
     } else if (ldpc::layered_slots_per_cta(c->host) > 0) {
         cand[nc++] = SCHED_SLOTS_V1;
+        if (ldpc::layered_pairs_exact(*p) && ldpc::layered_pairs_per_cta(c->host) > 0) cand[nc++] = SCHED_SLOTS_V2;
     }
     cand[nc++] = SCHED_STREAMING;
     uint8_t *bits = nullptr;

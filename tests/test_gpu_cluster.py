@@ -10,7 +10,7 @@ import torch
 from oracle import oracle as O
 from paper_1812_06545_gb300 import inputs as I
 from paper_1812_06545_gb300 import ldpc
-from tests.gpu_helpers import FP32_TOL, clopper_pearson, oracle_code, rel_err
+from tests.gpu_helpers import FP32_TOL, assert_binary16_close, binary16_band, clopper_pearson, oracle_code, rel_err
 
 pytestmark = pytest.mark.gpu
 BIG = "qc34x68_z384_s5"
@@ -49,13 +49,12 @@ def test_fp32_posterior_first_three_iterations(cuda_dev, form, name, n, eb):
 
 @pytest.mark.parametrize("form,name", [("flood_f16", BIG), ("cluster_f16", "qc12x24_z81_s2")])
 def test_fp16_messages_first_three_iterations(cuda_dev, form, name):
-    _, _, c, L = I.make_frames(name, 7, 1.75, 63, 64)
+    _, _, c, L = I.make_frames(name, 60, 1.75, 63, 64)
     oc = oracle_code(name)
     for T in (1, 2, 3):
         app, _, _ = run(name, form, L, cuda_dev, max_iter=T, early_exit=0)
-        ref, _, _, R = oc.spa_flood(L, T, early_exit=False, fp16_msgs=True, return_messages=True)
-        tol = FP32_TOL * np.maximum(1.0, np.abs(ref)) + 4 * 2.0 ** -11 * oc.incoming_message_sum(R)
-        assert (np.abs(app - ref) <= tol).all(), (name, T)
+        ref, band = binary16_band(oc, False, L, T, 4)
+        assert_binary16_close(app, ref, band, strict=T == 1, what=(name, T))
 
 
 def test_large_code_early_exit_and_fer(cuda_dev):

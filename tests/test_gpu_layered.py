@@ -72,7 +72,9 @@ def test_mixed_code_family_bit_exact(cuda_dev, name):
 def test_saturation_parameters(cuda_dev):
     name = "qc6x24_z54_s46"
     _, _, c, L = I.make_frames(name, 200, 3.0, 42, 43)
-    for msg_sat, app_sat, an, ash in ((15, 15, 3, 2), (31, 63, 7, 3), (63, 127, 1, 0)):
+    # the first three run on two codewords per thread in packed half precision (exact for
+    # them); alpha = 9/16 at msg_sat = 127 is not exact there and runs one codeword per thread
+    for msg_sat, app_sat, an, ash in ((15, 15, 3, 2), (31, 63, 7, 3), (63, 127, 1, 0), (127, 127, 9, 4)):
         q = O.quantize(L, 2.0, msg_sat)
         got = run(gpu_code(name), q, cuda_dev, max_iter=6, msg_sat=msg_sat, app_sat=app_sat, nms_alpha_num=an,
                   nms_alpha_shift=ash)

@@ -12,7 +12,7 @@ import torch
 
 from paper_1812_06545_gb300 import inputs as I
 from paper_1812_06545_gb300 import ldpc
-from tests.gpu_helpers import FP32_TOL, oracle_code, rel_err
+from tests.gpu_helpers import FP32_TOL, assert_binary16_close, binary16_band, oracle_code, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -56,11 +56,10 @@ def test_posterior_every_codeword_full_occupancy(cuda_dev, form, name, n, eb, h1
         assert (iters == T).all()
         assert np.array_equal(bits, (app < 0).astype(np.uint8))
         if h16:
-            ref, _, _, R = orc(L, T, early_exit=False, fp16_msgs=True, return_messages=True)
-            tol = FP32_TOL * np.maximum(1.0, np.abs(ref)) + h16 * 2.0 ** -11 * oc.incoming_message_sum(R)
-            d = np.abs(app - ref)
-            bad = np.argwhere(d > tol)
-            assert bad.size == 0, (form, name, T, bad[:5], (d - tol).max())
+            # binary16 band: every codeword after the first flooding iteration, all but the
+            # few in which rounding flips cascade otherwise
+            ref, band = binary16_band(oc, layered, L, T, h16)
+            assert_binary16_close(app, ref, band, strict=T == 1 and not layered, what=(form, name, T))
         else:
             ref, _, _ = orc(L, T, early_exit=False)
             err = rel_err(app, ref)

@@ -82,10 +82,14 @@ def test_same_alone_and_in_the_mix(cuda_dev):
 
 def check_against_oracle(jobs):
     """Every served request against the oracle: the int8 min-sum bit-exact (decisions and
-    iteration counts); the sum-product forms with identical decisions on >= 99.99 % of the
-    codewords (FP16: wherever both decoders converged), iteration counts of converged
-    codewords, and a frame error rate inside the oracle's 95 % interval over all requests."""
-    stats = {"flood_f32": [0, 0, 0, 0], "flood_f16": [0, 0, 0, 0]}   # mismatches, codewords, gpu/oracle errors
+    iteration counts); the sum-product forms, aggregated over all requests of a form, with
+    identical decisions on >= 99.99 % of the codewords (FP16: wherever both decoders
+    converged), the same iteration count on >= 99.9 % of the converged codewords with identical
+    decisions (FP16: 99.5 %, a binary16 rounding flip can move the iteration in which the
+    syndrome first clears by one), and a frame error rate inside the oracle's 95 % interval."""
+    # per form: decision mismatches, codewords compared, iteration mismatches, converged,
+    # GPU frame errors, oracle frame errors, codewords
+    stats = {"flood_f32": [0] * 7, "flood_f16": [0] * 7}
     for j in jobs:
         oc = oracle_code(j.name)
         L = j.llr.numpy()
@@ -98,19 +102,21 @@ def check_against_oracle(jobs):
         _, rb, ri = oc.spa_flood(L, 20, early_exit=True, fp16_msgs=f16)
         same = (bits == rb).all(axis=1)
         conv = ri < 20
-        assert (iters[conv & same] == ri[conv & same]).mean() >= 0.999 if (conv & same).any() else True
+        st = stats[j.form]
+        st[2] += int((iters[conv & same] != ri[conv & same]).sum())
+        st[3] += int((conv & same).sum())
         if f16:
             same = same[conv & (iters < 20)]
-        st = stats[j.form]
         st[0] += int((~same).sum())
         st[1] += len(same)
-        st[2] += int((bits != j.c).any(axis=1).sum())
-        st[3] += int((rb != j.c).any(axis=1).sum())
-    for form, (mism, tot, eg, eo) in stats.items():
-        if tot == 0:
+        st[4] += int((bits != j.c).any(axis=1).sum())
+        st[5] += int((rb != j.c).any(axis=1).sum())
+        st[6] += j.n
+    for form, (mism, tot, imism, nconv, eg, eo, n) in stats.items():
+        if n == 0:
             continue
         assert mism <= 1e-4 * tot, (form, mism, tot)
-        n = sum(j.n for j in jobs if j.form == form)
+        assert imism <= (5e-3 if form == "flood_f16" else 1e-3) * nconv, (form, imism, nconv)
         lo, hi = clopper_pearson(eo, n)
         assert lo <= eg / n <= hi, (form, eg, eo, n)
 
