@@ -42,11 +42,36 @@ CN_SOURCES = ("flood_kernels.cu", "ldpc_internal.h")
 SLOTS_SOURCES = ("flood_slots.cu", "slot_common.cuh", "ldpc_internal.h")
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments and blank lines (string and character literals kept),
+    so that a comment-only edit leaves the hash of the compiled code unchanged."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(ln.rstrip() for ln in "".join(out).splitlines() if ln.strip())
+
+
 def source_sha256(names):
+    """Hash of the comment-stripped sources a kernel is compiled from."""
     h = hashlib.sha256()
     for n in names:
-        with open(os.path.join(_CSRC, n), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(_CSRC, n), encoding="utf-8") as f:
+            h.update(strip_comments(f.read()).encode())
     return h.hexdigest()
 
 

@@ -30,6 +30,13 @@
 
 namespace ldpc {
 
+#ifndef LDPC_LSPA_REFILL_CHUNK
+#define LDPC_LSPA_REFILL_CHUNK 1  // channel values a thread requests at once when a slot takes a codeword
+#endif
+#ifndef LDPC_LSPA_KMAX
+#define LDPC_LSPA_KMAX 64  // most slots in one barrier group
+#endif
+
 // The FP32-message form keeps APP, Q and R in base-2 units (LLR x log2 e, set at the refill
 // and undone at the output), which spares the phi evaluations their scaling multiplies; the
 // FP16-message form stays in natural units, so that its stored binary16 message is the
@@ -288,13 +295,22 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
         return any;
     };
 
-    // a slot given codeword k loads APP = L (+0: no -0 in APP) and clears its messages
+    // a slot given codeword k loads APP = L (+0: no -0 in APP) and clears its messages; the
+    // channel values of a chunk are all requested before any is used
     auto refill = [&](int64_t k) {
         const float *L = a.llr + k * N;
-        for (int j = 0; j < nb; j++) {
-            const float v = __ldg(L + j * Z + r);
-            if (!isfinite(v)) atomicOr(cd->status, IN_NONFINITE);
-            A[j * Z + r] = kBase2<MsgT> ? fmaf(v, kSLog2e, 0.0f) : v + 0.0f;
+        constexpr int CH = LDPC_LSPA_REFILL_CHUNK;
+        for (int j0 = 0; j0 < nb; j0 += CH) {
+            float v[CH];
+#pragma unroll
+            for (int w = 0; w < CH; w++)
+                if (j0 + w < nb) v[w] = __ldg(L + (j0 + w) * Z + r);
+#pragma unroll
+            for (int w = 0; w < CH; w++)
+                if (j0 + w < nb) {
+                    if (!isfinite(v[w])) atomicOr(cd->status, IN_NONFINITE);
+                    A[(j0 + w) * Z + r] = kBase2<MsgT> ? fmaf(v[w], kSLog2e, 0.0f) : v[w] + 0.0f;
+                }
         }
         for (int b = 0; b < nnz; b++) Rc[b * Z + r] = MsgT(0.0f);
     };
@@ -393,7 +409,7 @@ static LspaShape lspa_shape(const CodeDev &h, int msg, int64_t cap = SLOTS_MAX)
     while (cmax > 0 && lspa_smem(h, msg, cmax) > limit) cmax--;
     if (cap >= 1 && cap < cmax) cmax = (int)cap;  // a small batch spreads over the SMs
     const int tmax = lspa_threads_for(h.dc_max, msg);
-    for (int K = 1; K <= cmax; K++) {
+    for (int K = 1; K <= cmax && K <= LDPC_LSPA_KMAX; K++) {
         const int tpg = ((K * h.Z + 31) / 32) * 32;
         int G = tmax / tpg;
         if (tpg > 32 && G > 15) G = 15;

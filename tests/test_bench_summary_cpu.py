@@ -87,3 +87,13 @@ def test_summary_drops_optional_sections_before_required_keys():
 
 def test_sig_rounds_floats_only():
     assert bench._sig({"a": [1.23456789, 7, "x"], "b": float("nan")}) == {"a": [1.235, 7, "x"], "b": None}
+
+
+def test_source_hash_ignores_comments_only():
+    a = 'int f(int x) { // add one\n  return x + 1; /* done */ }\nconst char *s = "// not a comment";\n'
+    b = '/* header */\nint f(int x) {\n  return x + 1; }\nconst char *s = "// not a comment";\n'
+    c = 'int f(int x) { return x + 2; }\nconst char *s = "// not a comment";\n'
+    assert bench.strip_comments(a).replace(" ", "").replace("\n", "") == \
+        bench.strip_comments(b).replace(" ", "").replace("\n", "")
+    assert '"// not a comment"' in bench.strip_comments(a)
+    assert bench.strip_comments(a) != bench.strip_comments(c)
