@@ -534,7 +534,8 @@ def summary_line(line: dict, details_path: str) -> dict:
         if "large_code" in f:
             gb["n26112_f16"] = f["large_code"]["cluster_f16"]["value"]
         extra = {"stream_f32_hbm_frac": f.get("stream_f32", {}).get("roofline", {}).get("frac"),
-                 "layered_i8_gedge_s": f.get("layered_i8", {}).get("edge_updates_per_s", 0) / 1e9}
+                 "layered_i8_gedge_s": f.get("layered_i8", {}).get("edge_updates_per_s", 0) / 1e9,
+                 "layered_i8_alu_frac": f.get("layered_i8", {}).get("roofline", {}).get("frac")}
         opt.append(("forms_gbps", gb))
         opt.append(("forms_extra", extra))
     out["details"] = details_path
@@ -1076,11 +1077,23 @@ def main():
         mixed = run_mixed(ldpc, dev, rank, world, args.steps, args.warmup, max_over_ranks, barrier)
         mixed_frames = mixed.pop("frames")
         forms["mixed_f16"] = mixed
+        i8_eps = float(lcode.E * lit_np.sum() * args.steps / (lms * 1e-3))
+        # integer-issue roofline of the min-sum (the survey's definition): every SM retires 128
+        # int32 lane operations per clock and an edge update takes about 13.5 of them (sub,
+        # saturate, abs, min1/min2 tracking, sign xor; select, scale, sign, add, saturate); the
+        # packed binary16 kernel does two codewords per lane operation, so its own ceiling is
+        # twice this one
+        i8_peak = n_sm * 128 * sm_mhz * 1e6 / 13.5
         forms["layered_i8"] = {"workload": LAYERED_WORKLOAD, "code": lw.code, "value": lv,
                                "ms_per_decode": lms / args.steps, "avg_iterations": float(lit_np.mean()),
                                "fer": {f"{lw.ebn0_db[0]:.2f}": float((lbits.cpu().numpy() != lframes[0][1])
                                                                      .any(axis=1).mean())},
-                               "edge_updates_per_s": float(lcode.E * lit_np.sum() * args.steps / (lms * 1e-3))}
+                               "edge_updates_per_s": i8_eps,
+                               "roofline": {"bound": "alu", "kernel": "k_layered_pairs", "achieved": i8_eps / 1e9,
+                                            "peak": i8_peak / 1e9, "unit": "Gedge/s", "frac": i8_eps / i8_peak,
+                                            "frac_of_packed_ceiling": i8_eps / (2 * i8_peak),
+                                            "peak_source": f"{n_sm} SMs x 128 int32 lanes per clock x {sm_mhz:.0f} MHz "
+                                                           f"/ 13.5 integer operations per edge update"}}
         line["forms"] = forms
 
     # ---------------- end to end through the C ABI with host buffers

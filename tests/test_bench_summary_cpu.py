@@ -28,7 +28,8 @@ def full_line():
         "gpu_launches": 140, "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "samples": 55, "reasons": []},
         "forms": {**{f: {"value": 5.75123456789, "fer": {k: 0.1 for k in per}, "roofline": roof} for f in
                      ("flood_f16", "layered_f32", "layered_f16", "stream_f32", "stream_f16", "plain_f32")},
-                  "layered_i8": {"value": 32.91234567, "edge_updates_per_s": 4.18123456e11},
+                  "layered_i8": {"value": 32.91234567, "edge_updates_per_s": 4.18123456e11,
+                                 "roofline": {"frac": 0.2161234}},
                   "mixed_f16": {"graph_info_gbps": 7.4123456, "eager_info_gbps": 7.3412345},
                   "large_code": {"cluster_f16": {"value": 2.75123456}}},
         "e2e": {"value": 4.9712345678, "unit": "Gbit/s", "h2d_bytes_per_step": 445906944,
