@@ -31,8 +31,10 @@
 // Each lane of a thread slot holds its own codeword: it converges, writes its outputs and is
 // refilled from the work counter independently of the other lane.
 #include <cuda_fp16.h>
+#include <string.h>
 
 #include "ldpc_internal.h"
+#include "layered_pairs.h"
 
 namespace ldpc {
 
@@ -51,21 +53,22 @@ namespace ldpc {
 #define LDPC_PAIRS_REFILL_CHUNK 4  // channel values a thread requests at once when a lane takes a codeword
 #endif
 
+// One launch decodes every codeword of up to MULTI_MAX_REQS requests of one code: the
+// codewords are the items of one work sequence (request i's codewords are items item0 ..
+// item0 + n_cw - 1), taken from a global work counter.
 struct LayeredPairArgs {
-    const void *llr;
     int llr_type;
     float scale;
-    int64_t n_cw;
+    int n_req;
+    int64_t n_items;
     int C2, K, TPG;        // thread slots (two codewords each), thread slots per group, threads per group
     int strideA, strideR;  // APP stride (half2 elements) and R stride (byte pairs) per thread slot
     int max_iter, early_exit, msg_sat, app_sat;
     // binary16 pairs: +-msg_sat, +-app_sat, alpha = alpha_num / 2^alpha_shift and -delta =
     // 2^-(alpha_shift + 1) - 1/2, in both halves
     uint32_t sat, nsat, appmax, appmin, alpha, ndelta;
-    uint8_t *bits;
-    int32_t *iters;
-    float *app_out;
     unsigned long long *next;
+    ReqDev reqs[MULTI_MAX_REQS];
 };
 
 __device__ __forceinline__ uint32_t h2u(__half2 x) { return *reinterpret_cast<uint32_t *>(&x); }
@@ -180,13 +183,13 @@ __device__ __forceinline__ uint32_t pair_parity(int dc, const EdgeAddr<TABLE> &e
 
 __device__ __forceinline__ int sat_q(int x, int s) { return max(-s, min(s, x)); }
 
-// Load codeword k into lane v of a thread slot, this thread's row r: APP = quantised LLRs (+0
-// for zero) at positions j*Z + r, R = 0 (biased byte 128) for every block; the channel values
-// of a chunk are all requested before any is used.  Kept out of line: it runs once per codeword
-// and its registers stay out of the check loop's allocation.
+// Load codeword k of request rq into lane v of a thread slot, this thread's row r: APP =
+// quantised LLRs (+0 for zero) at positions j*Z + r, R = 0 (biased byte 128) for every block;
+// the channel values of a chunk are all requested before any is used.
 LDPC_PAIRS_COLD void lpair_refill(const LayeredPairArgs &a, const CodeDev *__restrict__ cd, __half *Ah,
-                                          uint16_t *Rc, int v, int k, int r, int N, int Z, int nb, int nnz)
+                                          uint16_t *Rc, int v, int rq, int k, int r, int N, int Z, int nb, int nnz)
 {
+    const void *llr = a.reqs[rq].llr;
     constexpr int CH = LDPC_PAIRS_REFILL_CHUNK;
     for (int j0 = 0; j0 < nb; j0 += CH) {
         int q[CH];
@@ -194,7 +197,7 @@ LDPC_PAIRS_COLD void lpair_refill(const LayeredPairArgs &a, const CodeDev *__res
             int raw[CH];
 #pragma unroll
             for (int w = 0; w < CH; w++)
-                if (j0 + w < nb) raw[w] = static_cast<const int8_t *>(a.llr)[(int64_t)k * N + (j0 + w) * Z + r];
+                if (j0 + w < nb) raw[w] = static_cast<const int8_t *>(llr)[(int64_t)k * N + (j0 + w) * Z + r];
 #pragma unroll
             for (int w = 0; w < CH; w++)
                 if (j0 + w < nb) {
@@ -205,7 +208,7 @@ LDPC_PAIRS_COLD void lpair_refill(const LayeredPairArgs &a, const CodeDev *__res
             float in[CH];
 #pragma unroll
             for (int w = 0; w < CH; w++)
-                if (j0 + w < nb) in[w] = __ldg(static_cast<const float *>(a.llr) + (int64_t)k * N + (j0 + w) * Z + r);
+                if (j0 + w < nb) in[w] = __ldg(static_cast<const float *>(llr) + (int64_t)k * N + (j0 + w) * Z + r);
 #pragma unroll
             for (int w = 0; w < CH; w++)
                 if (j0 + w < nb) {
@@ -221,19 +224,20 @@ LDPC_PAIRS_COLD void lpair_refill(const LayeredPairArgs &a, const CodeDev *__res
     for (int b = 0; b < nnz; b++) reinterpret_cast<uint8_t *>(Rc + b * Z + r)[v] = 128;
 }
 
-// Write lane v's outputs for codeword k (row r's positions): hard decisions, the posterior
-// (if asked for), and, from row 0, the iteration count.  Out of line like lpair_refill.
-LDPC_PAIRS_COLD void lpair_output(const LayeredPairArgs &a, const __half *Ah, int v, int k, int t, int r,
+// Write lane v's outputs for codeword k of request rq (row r's positions): hard decisions, the
+// posterior (if asked for), and, from row 0, the iteration count.
+LDPC_PAIRS_COLD void lpair_output(const LayeredPairArgs &a, const __half *Ah, int v, int rq, int k, int t, int r,
                                           int N, int Z, int nb)
 {
-    uint8_t *Bo = a.bits + (int64_t)k * N;
-    float *Ao = a.app_out ? a.app_out + (int64_t)k * N : nullptr;
+    const ReqDev &q = a.reqs[rq];
+    uint8_t *Bo = q.bits + (int64_t)k * N;
+    float *Ao = q.app ? q.app + (int64_t)k * N : nullptr;
     for (int j = 0; j < nb; j++) {
         const __half x = Ah[2 * (j * Z + r) + v];
         Bo[j * Z + r] = (__half_as_ushort(x) & 0x8000u) ? 1 : 0;
         if (Ao) Ao[j * Z + r] = __half2float(x);
     }
-    if (r == 0) a.iters[k] = t;
+    if (r == 0) q.iters[k] = t;
 }
 
 // the barrier of one group (named barrier group + 1), or the warp when the group is one warp
@@ -245,13 +249,13 @@ __device__ __forceinline__ void pgroup_sync(int grp, int tpg)
         asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(tpg) : "memory");
 }
 
-// Table space (ints) ahead of the slots: the block-row pointers, the edge descriptors (two ints
-// per block), and with TABLE the APP offset table: entry b*Z + r (16 bits) is the byte offset
+// Table space (ints) ahead of the slots: the lanes' next and current requests, the block-row pointers, the
+// edge descriptors (two ints per block), and with TABLE the APP offset table: entry b*Z + r (16 bits) is the byte offset
 // 4 (j Z + (r + s) mod Z) of the position that row r of block b = (row l, column j, shift s)
 // reaches, for every thread slot of the CTA.
 __host__ __device__ inline int lpairs_tables_ints(int nnz, int mb, int Z, bool table)
 {
-    return mb + 1 + 2 * nnz + (table ? (nnz * Z + 1) / 2 : 0);
+    return 2 * SLOTS_MAX + mb + 1 + 2 * nnz + (table ? (nnz * Z + 1) / 2 : 0);  // + the lanes' requests
 }
 
 // Threads per CTA: up to 1024 for rows of degree <= 16; 768 above, where the register file
@@ -266,8 +270,10 @@ __global__ void __launch_bounds__(lpairs_threads(DMAX), 1) k_layered_pairs(const
     const int C2 = a.C2, K = a.K, TPG = a.TPG;
     int32_t *bad = reinterpret_cast<int32_t *>(smem);               // [2 * C2] unsatisfied check seen, per codeword
     int32_t *gany = bad + SLOTS_MAX;                                 // [groups][2] group vote
-    int64_t *fresh = reinterpret_cast<int64_t *>(gany + SLOTS_MAX);  // [2 * C2] next codeword per lane
-    int2 *t_ed = reinterpret_cast<int2 *>(fresh + SLOTS_MAX);
+    int64_t *fresh = reinterpret_cast<int64_t *>(gany + SLOTS_MAX);  // [2 * C2] next codeword per lane (request-local)
+    int32_t *sreq = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);   // [2 * C2] its request
+    int32_t *creq = sreq + SLOTS_MAX;  // [2 * C2] request of the codeword each lane decodes
+    int2 *t_ed = reinterpret_cast<int2 *>(creq + SLOTS_MAX);
     int32_t *t_rowptr = reinterpret_cast<int32_t *>(t_ed + nnz);
     uint16_t *t_off = reinterpret_cast<uint16_t *>(t_rowptr + mb + 1);
     __half2 *APPs = reinterpret_cast<__half2 *>(smem + slots_smem_head(lpairs_tables_ints(nnz, mb, Z, TABLE)));
@@ -291,11 +297,23 @@ __global__ void __launch_bounds__(lpairs_threads(DMAX), 1) k_layered_pairs(const
     const bool mine = u < K * Z && c < C2;  // a row of a thread slot (else an idle lane of the group)
     if (tid == 0)
         for (int i = 0; i < SLOTS_MAX; i++) gany[i] = 0;
+    // a lane's leader takes the next item of the work sequence and finds its request
+    auto grab = [&](int lane) {
+        const unsigned long long k = atomicAdd(a.next, 1ull);
+        int64_t loc = -1;
+        int rq = -1;
+        if (k < (unsigned long long)a.n_items) {
+            for (rq = 0; rq < a.n_req - 1; rq++)
+                if ((int64_t)k < a.reqs[rq].item0 + a.reqs[rq].n_cw) break;
+            loc = (int64_t)k - a.reqs[rq].item0;
+        }
+        fresh[lane] = loc;
+        sreq[lane] = rq;
+    };
     if (mine && r == 0) {
 #pragma unroll
         for (int v = 0; v < 2; v++) {
-            const unsigned long long k = atomicAdd(a.next, 1ull);
-            fresh[2 * c + v] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+            grab(2 * c + v);
             bad[2 * c + v] = 0;
         }
     }
@@ -322,12 +340,19 @@ __global__ void __launch_bounds__(lpairs_threads(DMAX), 1) k_layered_pairs(const
         return any;
     };
 
-    int cw[2];  // codeword in each lane (-1: empty; batches hold at most 2^31 codewords)
+    // a lane taking codeword fresh / sreq: its request is kept in shared memory (creq, read again
+    // at the output), not in registers
+    auto take = [&](int v) {
+        const int rqv = sreq[2 * c + v];
+        if (r == 0) creq[2 * c + v] = rqv;
+        lpair_refill(a, cd, Ah, Rc, v, rqv, (int)fresh[2 * c + v], r, N, Z, nb, nnz);
+    };
+    int cw[2];  // request-local codeword in each lane (-1: empty; requests hold at most 2^31)
     int t[2] = {0, 0};
 #pragma unroll
     for (int v = 0; v < 2; v++) {
         cw[v] = mine ? (int)fresh[2 * c + v] : -1;
-        if (cw[v] >= 0) lpair_refill(a, cd, Ah, Rc, v, cw[v], r, N, Z, nb, nnz);
+        if (cw[v] >= 0) take(v);
     }
     if (!group_any(cw[0] >= 0 || cw[1] >= 0)) return;
 
@@ -358,11 +383,8 @@ __global__ void __launch_bounds__(lpairs_threads(DMAX), 1) k_layered_pairs(const
         for (int v = 0; v < 2; v++) {
             done[v] = cw[v] >= 0 && ((a.early_exit && bad[2 * c + v] == 0) || t[v] >= a.max_iter);
             if (done[v]) {
-                lpair_output(a, Ah, v, cw[v], t[v], r, N, Z, nb);
-                if (r == 0) {
-                    const unsigned long long k = atomicAdd(a.next, 1ull);
-                    fresh[2 * c + v] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
-                }
+                lpair_output(a, Ah, v, creq[2 * c + v], cw[v], t[v], r, N, Z, nb);
+                if (r == 0) grab(2 * c + v);
             }
         }
         pgroup_sync(g, TPG);
@@ -372,7 +394,7 @@ __global__ void __launch_bounds__(lpairs_threads(DMAX), 1) k_layered_pairs(const
             if (done[v]) {
                 cw[v] = (int)fresh[2 * c + v];
                 t[v] = 0;
-                if (cw[v] >= 0) lpair_refill(a, cd, Ah, Rc, v, cw[v], r, N, Z, nb, nnz);
+                if (cw[v] >= 0) take(v);
             }
         }
         if (!group_any(cw[0] >= 0 || cw[1] >= 0)) break;
@@ -467,23 +489,36 @@ static cudaError_t launch_lpairs_d(const CodeDev &h, const CodeDev *d, const Lay
     return launch_lpairs_t<32, SATAPP>(h, d, a, ctas, s);
 }
 
-cudaError_t layered_pairs_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p, const void *llr,
-                                 int llr_type, int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out,
-                                 void *counter, cudaStream_t s)
+// Decode the codewords of n requests of one code (reqs[i].code all the same) in one launch.
+cudaError_t layered_pairs_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p,
+                                 const HostReq *reqs, int n, int llr_type, void *counter, cudaStream_t s)
 {
-    if (!layered_pairs_exact(p)) return cudaErrorInvalidValue;
+    if (!layered_pairs_exact(p) || n < 1 || n > MULTI_MAX_REQS) return cudaErrorInvalidValue;
+    LayeredPairArgs a;
+    memset(&a, 0, sizeof a);
+    int64_t items = 0;
+    for (int i = 0; i < n; i++) {
+        if (reqs[i].n_cw <= 0) continue;
+        ReqDev &q = a.reqs[a.n_req++];
+        q.llr = reqs[i].llr;
+        q.bits = reqs[i].bits;
+        q.iters = reqs[i].iters;
+        q.app = reqs[i].app;
+        q.n_cw = reqs[i].n_cw;
+        q.item0 = items;
+        items += reqs[i].n_cw;
+    }
+    if (items == 0) return cudaSuccess;
+    a.n_items = items;
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     // a small batch spreads over the SMs rather than filling a few CTAs' slots
-    const int64_t per_cta = (n_cw + nsm - 1) / nsm;
+    const int64_t per_cta = (items + nsm - 1) / nsm;
     const LpairShape sh = lpairs_shape(h, (per_cta + 1) / 2);
     if (sh.C2 < 1) return cudaErrorInvalidValue;
-    LayeredPairArgs a;
-    a.llr = llr;
     a.llr_type = llr_type;
     a.scale = p.llr_scale;
-    a.n_cw = n_cw;
     a.C2 = sh.C2;
     a.K = sh.K;
     a.TPG = sh.TPG;
@@ -494,8 +529,8 @@ cudaError_t layered_pairs_decode(const CodeDev &h, const CodeDev *d, const ldpc_
     a.msg_sat = p.msg_sat;
     a.app_sat = p.app_sat;
     auto pair = [](float x) {
-        const unsigned short h = __half_as_ushort(__float2half_rn(x));  // exact for these values
-        return (uint32_t)h | ((uint32_t)h << 16);
+        const unsigned short hb = __half_as_ushort(__float2half_rn(x));  // exact for these values
+        return (uint32_t)hb | ((uint32_t)hb << 16);
     };
     a.sat = pair((float)p.msg_sat);
     a.nsat = pair(-(float)p.msg_sat);
@@ -503,12 +538,9 @@ cudaError_t layered_pairs_decode(const CodeDev &h, const CodeDev *d, const ldpc_
     a.appmin = pair(-(float)p.app_sat);
     a.alpha = pair((float)p.nms_alpha_num / (float)(1 << p.nms_alpha_shift));
     a.ndelta = pair(1.0f / (float)(2 << p.nms_alpha_shift) - 0.5f);
-    a.bits = bits;
-    a.iters = iters;
-    a.app_out = app_out;
     a.next = static_cast<unsigned long long *>(counter);
     int64_t ctas = nsm;
-    const int64_t need = (n_cw + 2 * a.C2 - 1) / (2 * a.C2);
+    const int64_t need = (items + 2 * a.C2 - 1) / (2 * a.C2);
     if (need < ctas) ctas = need;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "ldpc_internal.h"
+#include "layered_pairs.h"
 
 namespace {
 
@@ -353,9 +354,11 @@ static cudaError_t layered_slots_any(const ldpc_code *c, const ldpc_decode_param
                                      int64_t n_cw, uint8_t *bits, int32_t *iters, float *app, void *ws,
                                      cudaStream_t s)
 {
-    return use_layered_pairs(c, &p)
-               ? ldpc::layered_pairs_decode(c->host, c->dev, p, llr, llr_type, n_cw, bits, iters, app, ws, s)
-               : ldpc::layered_slots_decode(c->host, c->dev, p, llr, llr_type, n_cw, bits, iters, app, ws, s);
+    if (use_layered_pairs(c, &p)) {
+        const ldpc::HostReq rq = {c, llr, n_cw, bits, iters, app};
+        return ldpc::layered_pairs_decode(c->host, c->dev, p, &rq, 1, llr_type, ws, s);
+    }
+    return ldpc::layered_slots_decode(c->host, c->dev, p, llr, llr_type, n_cw, bits, iters, app, ws, s);
 }
 
 // The layered sum-product always runs as persistent slots (check_params admits only codes
@@ -501,8 +504,24 @@ ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldp
                                                hr[i].iters, hr[i].app, ws, s);
     } else {
         e = cudaSuccess;
+        // the packed min-sum decodes all requests of one code in one launch (one work
+        // sequence); every other layered request gets a launch of its own (stream-ordered:
+        // the work counter is reused)
+        bool done_req[ldpc::MULTI_MAX_REQS] = {};
+        if (!use_layered_spa(p))
+            for (int i = 0; i < n_req && e == cudaSuccess; i++) {
+                if (done_req[i] || hr[i].n_cw <= 0 || !use_layered_pairs(hr[i].code, p)) continue;
+                ldpc::HostReq same[ldpc::MULTI_MAX_REQS];
+                int ns = 0;
+                for (int k = i; k < n_req; k++)
+                    if (!done_req[k] && hr[k].n_cw > 0 && hr[k].code == hr[i].code) {
+                        same[ns++] = hr[k];
+                        done_req[k] = true;
+                    }
+                e = ldpc::layered_pairs_decode(hr[i].code->host, hr[i].code->dev, *p, same, ns, llr_type, ws, s);
+            }
         for (int i = 0; i < n_req && e == cudaSuccess; i++)
-            if (hr[i].n_cw > 0)
+            if (hr[i].n_cw > 0 && !done_req[i])
                 e = use_layered_spa(p)
                         ? ldpc::layered_spa_decode(hr[i].code->host, hr[i].code->dev, *p,
                                                    static_cast<const float *>(hr[i].llr), hr[i].n_cw, hr[i].bits,

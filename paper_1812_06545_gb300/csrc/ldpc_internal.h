@@ -122,14 +122,6 @@ __host__ __device__ inline size_t slots_smem_head(int tbl_ints)
     return ((size_t)SLOTS_MAX * 16 + 16 + (size_t)tbl_ints * 4 + 15) & ~(size_t)15;
 }
 
-// Layered min-sum with two codewords per thread in packed half precision (layered_pairs.cu):
-// exact for the parameters layered_pairs_exact admits; codewords per CTA (0: code too large).
-bool layered_pairs_exact(const ldpc_decode_params &p);
-int layered_pairs_per_cta(const CodeDev &host);
-cudaError_t layered_pairs_decode(const CodeDev &host, const CodeDev *dev, const ldpc_decode_params &p, const void *llr,
-                                 int llr_type, int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out,
-                                 void *counter, cudaStream_t s);
-
 // Layered sum-product slot decoder (layered_spa.cu): slots per CTA (0: code too large).
 int layered_spa_slots_per_cta(const CodeDev &host, int msg);
 cudaError_t layered_spa_decode(const CodeDev &host, const CodeDev *dev, const ldpc_decode_params &p, const float *llr,

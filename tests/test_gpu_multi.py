@@ -155,3 +155,31 @@ def test_mixed_launch_against_the_oracle(cuda_dev, form):
             assert rel_err(app, ref).max() <= FP32_TOL, (form, name, rel_err(app, ref).max())
     # binary16 rounding flips that cascade: at most a few codewords of the launch
     assert outside <= F16_CASCADE_FRAC * sum(sizes), (form, outside)
+
+
+def test_layered_i8_many_requests_per_code_one_launch_each(cuda_dev):
+    # The packed int8 min-sum takes every request of one code into one launch (one work
+    # sequence over the requests' codewords): requests of two codes, interleaved in the call,
+    # cut at ragged points (one of a single codeword); every request bit-exact against the
+    # decode of the whole batch alone and against the integer oracle.
+    p = ldpc.params_for("layered_i8", max_iter=10)
+    specs = [("qc4x24_z81_s3", 3000, 3.5, [0, 1000, 1001, 2500, 3000]),
+             ("qc8x24_z54_s45", 900, 2.75, [0, 450, 899, 900])]
+    reqs, checks = [], []
+    for name, n, eb, cuts in specs:
+        code = gpu_code(name)
+        _, _, c, L = I.make_frames(name, n, eb, 121, 122)
+        x = torch.from_numpy(L).to(cuda_dev)
+        whole = ldpc.decode(code, p, x, app=True)
+        o = outputs(code, n, cuda_dev)
+        parts = [(code.handle, x[a:b], b - a, o[0][a:b], o[1][a:b], o[2][a:b]) for a, b in zip(cuts, cuts[1:])]
+        reqs.append(parts)
+        checks.append((name, L, o, whole))
+    mixed = [q for pair in zip(reqs[0], reqs[1] + [None] * 4) for q in pair if q is not None]
+    ldpc.ldpc_decode_multi(mixed, p)
+    torch.cuda.synchronize()
+    for name, L, o, whole in checks:
+        assert torch.equal(o[0], whole[0]) and torch.equal(o[1], whole[1]) and torch.equal(o[2], whole[2]), name
+        ra, rb, ri = oracle_code(name).nms_layered(O.quantize(L, 2.0, 31), 10, early_exit=True)
+        assert np.array_equal(o[1].cpu().numpy(), ri) and np.array_equal(o[0].cpu().numpy(), rb), name
+        assert np.array_equal(o[2].cpu().numpy().astype(np.int32), ra), name
