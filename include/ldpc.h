@@ -177,10 +177,10 @@ typedef struct {
  *   llr_type   applies to every request.
  *   workspace  >= ldpc_multi_workspace_size() bytes of device memory (work counters),
  *              256-byte aligned, or NULL for a stream-ordered allocation on `stream`.
- * The flooding forms run all slot-sized requests in one launch and each cluster-sized
- * request in a launch of its own.  The layered min-sum, where its two-codewords-per-thread
- * form applies (see ldpc_autotune), runs all requests of one code in one launch; the other
- * layered forms issue one persistent launch per request.  All launches go on `stream`. */
+ * The flooding forms run all slot-sized requests in one launch and the requests of each
+ * cluster-sized code in one launch per code; the layered min-sum runs the requests of each
+ * code in one launch per code; the layered sum-product issues one persistent launch per
+ * request.  All launches go on `stream`. */
 ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldpc_decode_params *p,
                               int32_t llr_type, void *workspace, size_t workspace_bytes, void *stream);
 

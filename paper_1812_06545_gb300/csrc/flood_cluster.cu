@@ -29,12 +29,11 @@ namespace ldpc {
 
 constexpr int CLUSTER_CTAS = 2;
 
+// One launch decodes every codeword of up to MULTI_MAX_REQS requests of one code: the codewords
+// are the items of one work sequence (request i's are items item0 .. item0 + n_cw - 1).
 struct ClusterArgs {
-    const float *llr;
-    uint8_t *bits;
-    int32_t *iters;
-    float *app_out;
-    int64_t n_cw;
+    int n_req;
+    int64_t n_items;
     unsigned long long *next;
     int row_split[CLUSTER_CTAS + 1];  // block rows [row_split[q], row_split[q+1]) belong to CTA q
     int ncols[CLUSTER_CTAS];          // block columns CTA q holds the posteriors of
@@ -43,7 +42,33 @@ struct ClusterArgs {
     int col_list[CLUSTER_CTAS][NB_MAX];  // CTA q's columns in place order
     int max_iter, early_exit;
     float X;
+    ReqDev reqs[MULTI_MAX_REQS];
 };
+
+// 32-bit shared::cluster addresses: the address of shared variable p in CTA `rank` of the
+// cluster, and loads through such an address (the CTA's own memory or the other's).  Posteriors
+// and messages are read this way, so an operand's address is one 32-bit add from a per-owner
+// base, whichever CTA holds it.
+__device__ __forceinline__ uint32_t cl_map(const void *p, unsigned rank)
+{
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(out)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return out;
+}
+__device__ __forceinline__ float cl_ld(const float *, uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ float cl_ld(const __half *, uint32_t addr)
+{
+    unsigned short v;
+    asm volatile("ld.shared::cluster.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+    return __half2float(__ushort_as_half(v));
+}
 
 __host__ __device__ inline int cl_owner(const int *split, int x)
 {
@@ -55,17 +80,18 @@ __host__ __device__ inline int cl_owner(const int *split, int x)
 // One check of an owned row: Q = APP - R over its edges (posteriors wherever they live), the
 // phi rule, messages written in place; returns the parity of the posteriors' sign bits.
 template <int D, bool EXACT, typename MsgT>
-__device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed, MsgT *Rr, const float *app_0,
-                                             const float *app_1, int r, int Z, float X, float Xb)
+__device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed, MsgT *Rr, uint32_t app_0,
+                                             uint32_t app_1, int r, int Z, float X, float Xb)
 {
     constexpr uint32_t kSign = 0x80000000u;
     float av[D];
     uint32_t sg = 0, par = 0;
+    const uint32_t rb = 4u * (uint32_t)r, ZA = 4u * (uint32_t)Z;
 #pragma unroll
     for (int k = 0; k < D; k++) {
         if (EXACT || k < dc) {
             const int4 d = ed[k];
-            const float ap = (d.z ? app_1 : app_0)[d.x + r - (r >= d.y ? Z : 0)];
+            const float ap = cl_ld((const float *)nullptr, (d.z ? app_1 : app_0) + d.x + rb - (r >= d.y ? ZA : 0u));
             const float qv = ap - (float)Rr[k * Z];
             par ^= __float_as_uint(ap);
             const uint32_t qs = __float_as_uint(qv) & kSign;
@@ -116,7 +142,7 @@ __device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed
 
 template <int D, int DMAX, typename MsgT>
 __device__ __forceinline__ uint32_t cl_check_dispatch(int dc, const int4 *__restrict__ ent, MsgT *Rr,
-                                                      const float *app_0, const float *app_1, int r, int Z, float X,
+                                                      uint32_t app_0, uint32_t app_1, int r, int Z, float X,
                                                       float Xb)
 {
     if constexpr (D >= DMAX) {
@@ -134,20 +160,22 @@ __device__ __forceinline__ uint32_t cl_check_dispatch(int dc, const int4 *__rest
 // descriptors cd, see the kernel) onto sum, in the order of the column lists: straight-line
 // bodies for the common degrees (every lane of a warp takes the same branch).
 template <int D, typename MsgT>
-__device__ __forceinline__ float cl_vn_sum(const int4 *__restrict__ cd, const MsgT *r_0, const MsgT *r_1, int c, int Z,
+__device__ __forceinline__ float cl_vn_sum(const int4 *__restrict__ cd, uint32_t r_0, uint32_t r_1, int c, int Z,
                                            float sum)
 {
+    constexpr uint32_t SZ = sizeof(MsgT);
 #pragma unroll
     for (int k = 0; k < D; k++) {
         const int4 d = cd[k];
-        sum += (float)(d.z ? r_1 : r_0)[d.x + c + (c < d.y ? Z : 0)];
+        sum += cl_ld((const MsgT *)nullptr, (d.z ? r_1 : r_0) + d.x + SZ * (uint32_t)c + (c < d.y ? SZ * Z : 0u));
     }
     return sum;
 }
 template <typename MsgT>
-__device__ __forceinline__ float cl_vn_column(int dv, const int4 *__restrict__ cd, const MsgT *r_0, const MsgT *r_1,
-                                              int c, int Z, float sum)
+__device__ __forceinline__ float cl_vn_column(int dv, const int4 *__restrict__ cd, uint32_t r_0, uint32_t r_1, int c,
+                                              int Z, float sum)
 {
+    constexpr uint32_t SZ = sizeof(MsgT);
     switch (dv) {
     case 2: return cl_vn_sum<2, MsgT>(cd, r_0, r_1, c, Z, sum);
     case 3: return cl_vn_sum<3, MsgT>(cd, r_0, r_1, c, Z, sum);
@@ -155,7 +183,7 @@ __device__ __forceinline__ float cl_vn_column(int dv, const int4 *__restrict__ c
     default:
         for (int k = 0; k < dv; k++) {
             const int4 d = cd[k];
-            sum += (float)(d.z ? r_1 : r_0)[d.x + c + (c < d.y ? Z : 0)];
+            sum += cl_ld((const MsgT *)nullptr, (d.z ? r_1 : r_0) + d.x + SZ * (uint32_t)c + (c < d.y ? SZ * Z : 0u));
         }
         return sum;
     }
@@ -184,7 +212,8 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
     const int Z = cd->Z, mb = cd->mb, nb = cd->nb, nnz = cd->nnz;
     const float X = a.X, Xb = a.X * kSLog2e;
 
-    // bookkeeping: [0] bad flags (2, alternating by round), [2] codeword (int64 at 8)
+    // bookkeeping: [0] bad flags (2, alternating by round), [2] the codeword being decoded
+    // (int64 at 8: request << 32 | request-local index, -1 when the work is done)
     int32_t *flags = reinterpret_cast<int32_t *>(smem);
     int64_t *cwp = reinterpret_cast<int64_t *>(smem + 8);
     int32_t *t_rowptr = reinterpret_cast<int32_t *>(smem + 16);  // [mb + 1]
@@ -206,7 +235,7 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
     for (int b = tid; b < nnz; b += nth) {
         const int e = cd->ent[b];
         const int j = e >> 16, s = e & 0xffff;
-        t_ed[b] = make_int4(a.col_slot[j] * Z + s, Z - s, a.col_owner[j], 0);
+        t_ed[b] = make_int4(4 * (a.col_slot[j] * Z + s), Z - s, a.col_owner[j], 0);
     }
     for (int i = tid; i < nnz; i += nth) {
         const int ce = cd->colent[i];
@@ -214,7 +243,7 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
         int l = 0;
         while (l < mb - 1 && b >= cd->rowptr[l + 1]) l++;
         const int qo = cl_owner(a.row_split, l);
-        t_cd[i] = make_int4((b - cd->rowptr[a.row_split[qo]]) * Z - s, s, qo, 0);
+        t_cd[i] = make_int4((int)sizeof(MsgT) * ((b - cd->rowptr[a.row_split[qo]]) * Z - s), s, qo, 0);
     }
     const size_t off_app = cl_tables_bytes(nnz);
     float *app = reinterpret_cast<float *>(smem + off_app);
@@ -227,9 +256,17 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
     // the cluster's posterior and message arrays, by owning CTA (generic pointers; the own
     // CTA's are plain shared memory)
     static_assert(CLUSTER_CTAS == 2, "the owner selects below assume two CTAs");
-    const float *app_0 = cluster.map_shared_rank(app, 0), *app_1 = cluster.map_shared_rank(app, 1);
-    const MsgT *r_0 = cluster.map_shared_rank(R, 0), *r_1 = cluster.map_shared_rank(R, 1);
-    const int n_check = (row1 - row0) * Z, n_var = a.ncols[q] * Z;
+    const uint32_t app_0 = cl_map(app, 0), app_1 = cl_map(app, 1);
+    const uint32_t r_0 = cl_map(R, 0), r_1 = cl_map(R, 1);
+    const int n_var = a.ncols[q] * Z;
+    // The check and variable loops without a division per item: thread tid works on position
+    // tid mod Z of block rows / columns tid / Z, tid / Z + RS, ... (RS = nth / Z rows per pass;
+    // threads beyond RS * Z idle there).  When Z exceeds the thread count (RS = 0), thread tid
+    // works on positions tid, tid + nth, ... of every block row / column instead.
+    const int RS = nth / Z;
+    const int p0 = RS > 0 ? tid % Z : tid, ps = RS > 0 ? Z : nth;     // positions
+    const int l0 = RS > 0 ? tid / Z : 0, ls = RS > 0 ? RS : 1;        // block rows / columns
+    const bool works = RS == 0 || tid / Z < RS;
     const int *my_cols = a.col_list[q];
     int64_t *cw0 = cluster.map_shared_rank(cwp, 0);
     cluster.sync();  // tables built in every CTA before any remote access
@@ -238,14 +275,22 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
         // the leader (CTA 0, thread 0) takes the next codeword; every CTA reads it
         if (q == 0 && tid == 0) {
             const unsigned long long k = atomicAdd(a.next, 1ull);
-            cwp[0] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+            int64_t v = -1;
+            if (k < (unsigned long long)a.n_items) {
+                int rq = 0;
+                while (rq < a.n_req - 1 && (int64_t)k >= a.reqs[rq].item0 + a.reqs[rq].n_cw) rq++;
+                v = ((int64_t)rq << 32) | ((int64_t)k - a.reqs[rq].item0);
+            }
+            cwp[0] = v;
         }
         cluster.sync();  // also: no CTA still reads another's flags of the previous codeword
-        const int64_t cw = *cw0;
-        if (cw < 0) break;
+        const int64_t item = *cw0;
+        if (item < 0) break;
+        const ReqDev &req = a.reqs[(int)(item >> 32)];
+        const int64_t cw = item & 0xffffffffll;
         if (tid == 0) flags[0] = flags[1] = 0;
         // load: APP = L (+0: no -0) for owned variables, R = 0 for owned edges
-        const float *L = a.llr + cw * cd->N;
+        const float *L = static_cast<const float *>(req.llr) + cw * cd->N;
         for (int i = tid; i < n_var; i += nth) {
             const int jl = i / Z, c = i - jl * Z;
             const float v = __ldg(L + my_cols[jl] * Z + c);
@@ -260,15 +305,16 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
             const int tr = t;  // this round's flag is flags[tr & 1]
             // ---------------- check-node phase over the owned checks
             bool pbad = false;
-            for (int w = tid; w < n_check; w += nth) {
-                const int lr = w / Z, r = w - lr * Z;
+            auto check_row = [&](int lr, int r) {
                 const int l = row0 + lr;
                 const int b0 = t_rowptr[l];
                 const uint32_t par = cl_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0,
                                                                       R + (b0 - blk0) * Z + r, app_0, app_1, r, Z,
                                                                       X, Xb);
                 pbad |= (par & kSign) != 0;
-            }
+            };
+            for (int r = p0; works && r < Z; r += ps)
+                for (int lr = l0; lr < row1 - row0; lr += ls) check_row(lr, r);
             if (pbad) flags[tr & 1] = 1;
             cluster.sync();
             // ---------------- decision (the same in every CTA: all flags are read after the barrier)
@@ -278,14 +324,15 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
             const bool conv = tr >= 1 && a.early_exit && !any_bad;
             if (!conv) {
                 // ---------------- variable-node phase over the owned variables
-                for (int i = tid; i < n_var; i += nth) {
-                    const int jl = i / Z, c = i - jl * Z;
+                auto var_col = [&](int jl, int c) {
                     const int j = my_cols[jl];
                     const int e0 = t_colptr[j];
                     const float sum = cl_vn_column<MsgT>(t_colptr[j + 1] - e0, t_cd + e0, r_0, r_1, c, Z,
                                                          __ldg(L + j * Z + c));
-                    app[i] = sum + 0.0f;  // -0 -> +0: the sign bit is the decision
-                }
+                    app[jl * Z + c] = sum + 0.0f;  // -0 -> +0: the sign bit is the decision
+                };
+                for (int c = p0; works && c < Z; c += ps)
+                    for (int jl = l0; jl < a.ncols[q]; jl += ls) var_col(jl, c);
                 t++;
             }
             done = conv || t >= a.max_iter;
@@ -295,8 +342,8 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
             cluster.sync();
         }
         // output: each CTA writes its variables
-        uint8_t *Bo = a.bits + cw * cd->N;
-        float *Ao = a.app_out ? a.app_out + cw * cd->N : nullptr;
+        uint8_t *Bo = req.bits + cw * cd->N;
+        float *Ao = req.app ? req.app + cw * cd->N : nullptr;
         for (int i = tid; i < n_var; i += nth) {
             const int jl = i / Z, c = i - jl * Z;
             const int n = my_cols[jl] * Z + c;
@@ -304,7 +351,7 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
             Bo[n] = v < 0.0f ? 1 : 0;
             if (Ao) Ao[n] = v;
         }
-        if (q == 0 && tid == 0) a.iters[cw] = t;
+        if (q == 0 && tid == 0) req.iters[cw] = t;
     }
     cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
@@ -434,19 +481,28 @@ static cudaError_t launch_cluster(const ClusterArgs &a, size_t smem, int64_t n_c
     return cudaGetLastError();
 }
 
-cudaError_t flood_cluster_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p, const float *llr,
-                                 int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out, void *counter,
-                                 cudaStream_t s)
+cudaError_t flood_cluster_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p, const HostReq *reqs,
+                                 int n, void *counter, cudaStream_t s)
 {
+    if (n < 1 || n > MULTI_MAX_REQS) return cudaErrorInvalidValue;
     ClusterArgs a;
     memset(&a, 0, sizeof a);
     const size_t smem = cl_plan(h, p.msg, a, cl_limit());
     if (smem == 0) return cudaErrorInvalidValue;
-    a.llr = llr;
-    a.bits = bits;
-    a.iters = iters;
-    a.app_out = app_out;
-    a.n_cw = n_cw;
+    int64_t items = 0;
+    for (int i = 0; i < n; i++) {
+        if (reqs[i].n_cw <= 0) continue;
+        ReqDev &q = a.reqs[a.n_req++];
+        q.llr = reqs[i].llr;
+        q.bits = reqs[i].bits;
+        q.iters = reqs[i].iters;
+        q.app = reqs[i].app;
+        q.n_cw = reqs[i].n_cw;
+        q.item0 = items;
+        items += reqs[i].n_cw;
+    }
+    if (items == 0) return cudaSuccess;
+    a.n_items = items;
     a.next = static_cast<unsigned long long *>(counter);
     a.max_iter = p.max_iter;
     a.early_exit = p.early_exit;
@@ -455,10 +511,10 @@ cudaError_t flood_cluster_decode(const CodeDev &h, const CodeDev *d, const ldpc_
     if (e != cudaSuccess) return e;
     const bool f16 = p.msg == LDPC_MSG_F16;
     if (h.dc_max <= 8)
-        return f16 ? launch_cluster<8, __half>(a, smem, n_cw, d, s) : launch_cluster<8, float>(a, smem, n_cw, d, s);
+        return f16 ? launch_cluster<8, __half>(a, smem, items, d, s) : launch_cluster<8, float>(a, smem, items, d, s);
     if (h.dc_max <= 16)
-        return f16 ? launch_cluster<16, __half>(a, smem, n_cw, d, s) : launch_cluster<16, float>(a, smem, n_cw, d, s);
-    return f16 ? launch_cluster<32, __half>(a, smem, n_cw, d, s) : launch_cluster<32, float>(a, smem, n_cw, d, s);
+        return f16 ? launch_cluster<16, __half>(a, smem, items, d, s) : launch_cluster<16, float>(a, smem, items, d, s);
+    return f16 ? launch_cluster<32, __half>(a, smem, items, d, s) : launch_cluster<32, float>(a, smem, items, d, s);
 }
 
 }  // namespace ldpc

@@ -19,6 +19,8 @@
 //   APP_n = sat(Q_k + R_k, app_sat)
 // After every iteration the hard decisions [APP < 0] are checked against all checks; a
 // codeword with zero syndrome stops and reports that iteration (early exit).
+#include <string.h>
+
 #include "ldpc_internal.h"
 
 namespace ldpc {
@@ -187,17 +189,17 @@ __global__ void __launch_bounds__(512) k_layered_nms(const CodeDev *__restrict__
 // variable-node pass).  After every full iteration each slot's hard decisions are checked
 // against all of its checks; a slot that converged (or reached max_iter) writes its outputs
 // and takes the next codeword from the global work counter at the group's next iteration.
+// One launch decodes every codeword of up to MULTI_MAX_REQS requests of one code, the items of
+// one work sequence (request i's codewords are items item0 .. item0 + n_cw - 1).
 struct LayeredSlotArgs {
-    const void *llr;
     int llr_type;
     float scale;
-    int64_t n_cw;
+    int n_req;
+    int64_t n_items;
     int C, K, TPG, strideA, strideR;  // slots, slots per group, threads per group, strides
     int max_iter, early_exit, alpha_num, alpha_shift, msg_sat, app_sat;
-    uint8_t *bits;
-    int32_t *iters;
-    float *app_out;
     unsigned long long *next;
+    ReqDev reqs[MULTI_MAX_REQS];
 };
 
 // The barrier of one group: its warps only (named barrier group + 1; barrier 0 is the CTA's),
@@ -243,22 +245,25 @@ __device__ __forceinline__ unsigned lslots_row_parity(int dc, const int2 *__rest
     }
 }
 
-// Table space (ints) ahead of the slots: two per block for its edge descriptor, then the
-// block-row pointers.
-__host__ __device__ inline int lslots_tables_ints(int nnz, int mb) { return 2 * nnz + mb + 1; }
+// Table space (ints) ahead of the slots: the slots' next and current requests, two per block for
+// its edge descriptor, then the block-row pointers.
+__host__ __device__ inline int lslots_tables_ints(int nnz, int mb) { return 2 * SLOTS_MAX + 2 * nnz + mb + 1; }
 
 template <int DMAX>
-__global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__restrict__ cd, LayeredSlotArgs a)
+__global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__restrict__ cd,
+                                                           const __grid_constant__ LayeredSlotArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int N = cd->N, Z = cd->Z, mb = cd->mb, nb = cd->nb, nnz = cd->nnz;
     const int C = a.C, K = a.K, TPG = a.TPG;
     int32_t *bad = reinterpret_cast<int32_t *>(smem);                 // [SLOTS_MAX] unsatisfied check seen
     int32_t *gany = bad + SLOTS_MAX;                                   // [SLOTS_MAX / 2][2] group vote
-    int64_t *fresh = reinterpret_cast<int64_t *>(gany + SLOTS_MAX);    // [SLOTS_MAX]
+    int64_t *fresh = reinterpret_cast<int64_t *>(gany + SLOTS_MAX);    // [SLOTS_MAX] next codeword (request-local)
+    int32_t *sreq = reinterpret_cast<int32_t *>(fresh + SLOTS_MAX);    // [SLOTS_MAX] its request
+    int32_t *creq = sreq + SLOTS_MAX;                                   // [SLOTS_MAX] request being decoded
     // edge descriptor of block b = (row l, column j, shift s): .x = j*Z + s, .y = Z - s; check
     // row r reaches APP offset r + .x, less Z when r >= .y (position (r + s) mod Z of column j)
-    int2 *t_ed = reinterpret_cast<int2 *>(fresh + SLOTS_MAX);
+    int2 *t_ed = reinterpret_cast<int2 *>(creq + SLOTS_MAX);
     int32_t *t_rowptr = reinterpret_cast<int32_t *>(t_ed + nnz);
     int8_t *APPs = reinterpret_cast<int8_t *>(smem + slots_smem_head(lslots_tables_ints(nnz, mb)));
     int8_t *Rs = APPs + (size_t)C * a.strideA;
@@ -274,9 +279,21 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
     const bool mine = u < K * Z && c < C;  // a row of a slot (else an idle lane of the group)
     if (tid == 0)
         for (int i = 0; i < SLOTS_MAX; i++) gany[i] = 0;
-    if (mine && r == 0) {
+    // a slot's leader takes the next item of the work sequence and finds its request
+    auto grab = [&]() {
         const unsigned long long k = atomicAdd(a.next, 1ull);
-        fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+        int64_t loc = -1;
+        int rq = -1;
+        if (k < (unsigned long long)a.n_items) {
+            for (rq = 0; rq < a.n_req - 1; rq++)
+                if ((int64_t)k < a.reqs[rq].item0 + a.reqs[rq].n_cw) break;
+            loc = (int64_t)k - a.reqs[rq].item0;
+        }
+        fresh[c] = loc;
+        sreq[c] = rq;
+    };
+    if (mine && r == 0) {
+        grab();
         bad[c] = 0;
     }
     __syncthreads();
@@ -296,16 +313,20 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
         return any;
     };
 
+    // load codeword k of request rq (the request is kept in shared memory, creq, for the output)
     auto refill = [&](int64_t k) {
+        const int rq = sreq[c];
+        if (r == 0) creq[c] = rq;
+        const void *llr = a.reqs[rq].llr;
         for (int j = 0; j < nb; j++) {
             const int64_t i = k * N + j * Z + r;
             int q;
             if (a.llr_type == LDPC_LLR_I8) {
-                const int raw = static_cast<const int8_t *>(a.llr)[i];
+                const int raw = static_cast<const int8_t *>(llr)[i];
                 if (raw < -a.msg_sat || raw > a.msg_sat) atomicOr(cd->status, IN_I8_RANGE);
                 q = sat_i(raw, a.msg_sat);
             } else {
-                const float in = __ldg(static_cast<const float *>(a.llr) + i);
+                const float in = __ldg(static_cast<const float *>(llr) + i);
                 if (!isfinite(in)) atomicOr(cd->status, IN_NONFINITE);
                 const float rr = rintf(__fmul_rn(a.scale, in));
                 q = rr > (float)a.msg_sat ? a.msg_sat : (rr < -(float)a.msg_sat ? -a.msg_sat : (int)rr);
@@ -377,17 +398,17 @@ __global__ void __launch_bounds__(1024, 1) k_layered_slots(const CodeDev *__rest
         if (busy) {
             done = (a.early_exit && bad[c] == 0) || t >= a.max_iter;
             if (done) {
-                uint8_t *Bo = a.bits + cw * N;
-                float *Ao = a.app_out ? a.app_out + cw * N : nullptr;
+                const ReqDev &q = a.reqs[creq[c]];
+                uint8_t *Bo = q.bits + cw * N;
+                float *Ao = q.app ? q.app + cw * N : nullptr;
                 for (int j = 0; j < nb; j++) {
                     const int v = A[j * Z + r];
                     Bo[j * Z + r] = v < 0 ? 1 : 0;
                     if (Ao) Ao[j * Z + r] = (float)v;
                 }
                 if (r == 0) {
-                    a.iters[cw] = t;
-                    const unsigned long long k = atomicAdd(a.next, 1ull);
-                    fresh[c] = k < (unsigned long long)a.n_cw ? (int64_t)k : -1;
+                    q.iters[cw] = t;
+                    grab();
                 }
             }
         }
@@ -470,7 +491,7 @@ static cudaError_t launch_lslots(const CodeDev &h, const CodeDev *d, const Layer
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int64_t ctas = nsm;
-    const int64_t need = (a.n_cw + a.C - 1) / a.C;
+    const int64_t need = (a.n_items + a.C - 1) / a.C;
     if (need < ctas) ctas = need;
     LaunchScope ls(F_LAYERED, s);
     const int groups = (a.C + a.K - 1) / a.K;
@@ -478,19 +499,33 @@ static cudaError_t launch_lslots(const CodeDev &h, const CodeDev *d, const Layer
     return cudaGetLastError();
 }
 
-cudaError_t layered_slots_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p, const void *llr,
-                                 int llr_type, int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out,
-                                 void *counter, cudaStream_t s)
+// Decode the codewords of n requests of one code (reqs[i].code all the same) in one launch.
+cudaError_t layered_slots_decode(const CodeDev &h, const CodeDev *d, const ldpc_decode_params &p, const HostReq *reqs,
+                                 int n, int llr_type, void *counter, cudaStream_t s)
 {
+    if (n < 1 || n > MULTI_MAX_REQS) return cudaErrorInvalidValue;
     LayeredSlotArgs a;
-    a.llr = llr;
+    memset(&a, 0, sizeof a);
+    int64_t items = 0;
+    for (int i = 0; i < n; i++) {
+        if (reqs[i].n_cw <= 0) continue;
+        ReqDev &q = a.reqs[a.n_req++];
+        q.llr = reqs[i].llr;
+        q.bits = reqs[i].bits;
+        q.iters = reqs[i].iters;
+        q.app = reqs[i].app;
+        q.n_cw = reqs[i].n_cw;
+        q.item0 = items;
+        items += reqs[i].n_cw;
+    }
+    if (items == 0) return cudaSuccess;
+    a.n_items = items;
     a.llr_type = llr_type;
     a.scale = p.llr_scale;
-    a.n_cw = n_cw;
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const LslotShape sh = lslots_shape(h, (n_cw + nsm - 1) / nsm);
+    const LslotShape sh = lslots_shape(h, (items + nsm - 1) / nsm);
     a.C = sh.C;
     if (a.C < 1) return cudaErrorInvalidValue;
     a.K = sh.K;
@@ -503,9 +538,6 @@ cudaError_t layered_slots_decode(const CodeDev &h, const CodeDev *d, const ldpc_
     a.alpha_shift = p.nms_alpha_shift;
     a.msg_sat = p.msg_sat;
     a.app_sat = p.app_sat;
-    a.bits = bits;
-    a.iters = iters;
-    a.app_out = app_out;
     a.next = static_cast<unsigned long long *>(counter);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;

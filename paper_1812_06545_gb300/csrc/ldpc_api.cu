@@ -354,11 +354,9 @@ static cudaError_t layered_slots_any(const ldpc_code *c, const ldpc_decode_param
                                      int64_t n_cw, uint8_t *bits, int32_t *iters, float *app, void *ws,
                                      cudaStream_t s)
 {
-    if (use_layered_pairs(c, &p)) {
-        const ldpc::HostReq rq = {c, llr, n_cw, bits, iters, app};
-        return ldpc::layered_pairs_decode(c->host, c->dev, p, &rq, 1, llr_type, ws, s);
-    }
-    return ldpc::layered_slots_decode(c->host, c->dev, p, llr, llr_type, n_cw, bits, iters, app, ws, s);
+    const ldpc::HostReq rq = {c, llr, n_cw, bits, iters, app};
+    return use_layered_pairs(c, &p) ? ldpc::layered_pairs_decode(c->host, c->dev, p, &rq, 1, llr_type, ws, s)
+                                    : ldpc::layered_slots_decode(c->host, c->dev, p, &rq, 1, llr_type, ws, s);
 }
 
 // The layered sum-product always runs as persistent slots (check_params admits only codes
@@ -427,8 +425,8 @@ ldpc_status ldpc_decode_batch(const ldpc_code *c, const ldpc_decode_params *p, c
         const ldpc::HostReq rq = {c, llr, n_cw, bits, iters, app};
         e = ldpc::flood_multi_decode(&rq, 1, *p, ws, s);
     } else if (use_cluster(c, p)) {
-        e = ldpc::flood_cluster_decode(c->host, c->dev, *p, static_cast<const float *>(llr), n_cw, bits, iters, app,
-                                       ws, s);
+        const ldpc::HostReq rq = {c, llr, n_cw, bits, iters, app};
+        e = ldpc::flood_cluster_decode(c->host, c->dev, *p, &rq, 1, ws, s);
     } else {
         ldpc::FloodWs w;
         ldpc::flood_ws_layout(c->host, n_cw, p->msg, &w, static_cast<char *>(ws));
@@ -497,20 +495,28 @@ ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldp
         for (int i = 0; i < n_req; i++)
             if (hr[i].n_cw > 0 && use_slots(hr[i].code, p)) small[ns++] = hr[i];
         e = ns ? ldpc::flood_multi_decode(small, ns, *p, ws, s) : cudaSuccess;
-        for (int i = 0; i < n_req && e == cudaSuccess; i++)
-            if (hr[i].n_cw > 0 && !use_slots(hr[i].code, p))
-                e = ldpc::flood_cluster_decode(hr[i].code->host, hr[i].code->dev, *p,
-                                               static_cast<const float *>(hr[i].llr), hr[i].n_cw, hr[i].bits,
-                                               hr[i].iters, hr[i].app, ws, s);
+        // cluster-sized codes: one launch per code over all its requests
+        bool done_req[ldpc::MULTI_MAX_REQS] = {};
+        for (int i = 0; i < n_req && e == cudaSuccess; i++) {
+            if (done_req[i] || hr[i].n_cw <= 0 || use_slots(hr[i].code, p)) continue;
+            ldpc::HostReq same[ldpc::MULTI_MAX_REQS];
+            int nsame = 0;
+            for (int k = i; k < n_req; k++)
+                if (!done_req[k] && hr[k].n_cw > 0 && hr[k].code == hr[i].code) {
+                    same[nsame++] = hr[k];
+                    done_req[k] = true;
+                }
+            e = ldpc::flood_cluster_decode(hr[i].code->host, hr[i].code->dev, *p, same, nsame, ws, s);
+        }
     } else {
         e = cudaSuccess;
-        // the packed min-sum decodes all requests of one code in one launch (one work
-        // sequence); every other layered request gets a launch of its own (stream-ordered:
-        // the work counter is reused)
+        // the min-sum decodes all requests of one code in one launch (one work sequence); the
+        // layered sum-product gives every request a launch of its own (stream-ordered: the work
+        // counter is reused)
         bool done_req[ldpc::MULTI_MAX_REQS] = {};
         if (!use_layered_spa(p))
             for (int i = 0; i < n_req && e == cudaSuccess; i++) {
-                if (done_req[i] || hr[i].n_cw <= 0 || !use_layered_pairs(hr[i].code, p)) continue;
+                if (done_req[i] || hr[i].n_cw <= 0) continue;
                 ldpc::HostReq same[ldpc::MULTI_MAX_REQS];
                 int ns = 0;
                 for (int k = i; k < n_req; k++)
@@ -518,16 +524,15 @@ ldpc_status ldpc_decode_multi(const ldpc_request *reqs, int32_t n_req, const ldp
                         same[ns++] = hr[k];
                         done_req[k] = true;
                     }
-                e = ldpc::layered_pairs_decode(hr[i].code->host, hr[i].code->dev, *p, same, ns, llr_type, ws, s);
+                const ldpc_code *c = hr[i].code;
+                e = use_layered_pairs(c, p) ? ldpc::layered_pairs_decode(c->host, c->dev, *p, same, ns, llr_type, ws, s)
+                                            : ldpc::layered_slots_decode(c->host, c->dev, *p, same, ns, llr_type, ws, s);
             }
         for (int i = 0; i < n_req && e == cudaSuccess; i++)
             if (hr[i].n_cw > 0 && !done_req[i])
-                e = use_layered_spa(p)
-                        ? ldpc::layered_spa_decode(hr[i].code->host, hr[i].code->dev, *p,
-                                                   static_cast<const float *>(hr[i].llr), hr[i].n_cw, hr[i].bits,
-                                                   hr[i].iters, hr[i].app, ws, s)
-                        : layered_slots_any(hr[i].code, *p, hr[i].llr, llr_type, hr[i].n_cw, hr[i].bits,
-                                            hr[i].iters, hr[i].app, ws, s);
+                e = ldpc::layered_spa_decode(hr[i].code->host, hr[i].code->dev, *p,
+                                             static_cast<const float *>(hr[i].llr), hr[i].n_cw, hr[i].bits,
+                                             hr[i].iters, hr[i].app, ws, s);
     }
     if (own) {
         cudaError_t e2 = cudaFreeAsync(ws, s);

@@ -69,11 +69,11 @@ cudaError_t layered_decode(const CodeDev &host, const CodeDev *dev, const ldpc_d
                            int llr_type, int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out,
                            cudaStream_t s);
 int layered_supported(const CodeDev &host);
-// Persistent slot form of the layered min-sum (0 slots: code too large for it).
+// Persistent slot form of the layered min-sum (0 slots: code too large for it); every codeword
+// of n requests of one code in one launch.
 int layered_slots_per_cta(const CodeDev &host);
-cudaError_t layered_slots_decode(const CodeDev &host, const CodeDev *dev, const ldpc_decode_params &p, const void *llr,
-                                 int llr_type, int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out,
-                                 void *counter, cudaStream_t s);
+cudaError_t layered_slots_decode(const CodeDev &host, const CodeDev *dev, const ldpc_decode_params &p,
+                                 const struct HostReq *reqs, int n, int llr_type, void *counter, cudaStream_t s);
 
 // ---------------------------------------------------------------- slot decoders
 // Persistent decoders with per-codeword work queues (flood_slots.cu, layered_kernels.cu).
@@ -129,11 +129,10 @@ cudaError_t layered_spa_decode(const CodeDev &host, const CodeDev *dev, const ld
                                cudaStream_t s);
 
 // Flooding SPA cluster decoder (flood_cluster.cu): one codeword per two-SM cluster, for codes
-// whose codeword does not fit one CTA.
+// whose codeword does not fit one CTA; every codeword of n requests of one code in one launch.
 int cluster_supported(const CodeDev &host, int msg);
-cudaError_t flood_cluster_decode(const CodeDev &host, const CodeDev *dev, const ldpc_decode_params &p, const float *llr,
-                                 int64_t n_cw, uint8_t *bits, int32_t *iters, float *app_out, void *counter,
-                                 cudaStream_t s);
+cudaError_t flood_cluster_decode(const CodeDev &host, const CodeDev *dev, const ldpc_decode_params &p,
+                                 const HostReq *reqs, int n, void *counter, cudaStream_t s);
 
 // Flooding SPA slot decoder: supported when one codeword of the code fits a CTA.
 int slots_supported(const CodeDev &host, int msg);

@@ -183,3 +183,27 @@ def test_layered_i8_many_requests_per_code_one_launch_each(cuda_dev):
         ra, rb, ri = oracle_code(name).nms_layered(O.quantize(L, 2.0, 31), 10, early_exit=True)
         assert np.array_equal(o[1].cpu().numpy(), ri) and np.array_equal(o[0].cpu().numpy(), rb), name
         assert np.array_equal(o[2].cpu().numpy().astype(np.int32), ra), name
+
+
+def test_large_code_requests_share_a_launch(cuda_dev):
+    # requests of the N = 26112 code (too large for the slot decoders): the FP16 flooding
+    # requests share one cluster-decoder launch and the int8 min-sum requests one launch of the
+    # one-codeword-per-thread kernel; every request equals its lone decode, and the int8 ones
+    # the integer oracle bit for bit
+    name = "qc34x68_z384_s5"
+    code = gpu_code(name)
+    _, _, c, L = I.make_frames(name, 23, 2.25, 131, 132)
+    x = torch.from_numpy(L).to(cuda_dev)
+    cuts = [0, 5, 6, 23]
+    for form in ("flood_f16", "layered_i8"):
+        p = ldpc.params_for(form, max_iter=10 if form == "layered_i8" else 20)
+        whole = ldpc.decode(code, p, x, app=True)
+        o = outputs(code, len(L), cuda_dev)
+        reqs = [(code.handle, x[a:b], b - a, o[0][a:b], o[1][a:b], o[2][a:b]) for a, b in zip(cuts, cuts[1:])]
+        ldpc.ldpc_decode_multi(reqs, p)
+        torch.cuda.synchronize()
+        assert torch.equal(o[0], whole[0]) and torch.equal(o[1], whole[1]) and torch.equal(o[2], whole[2]), form
+        if form == "layered_i8":
+            ra, rb, ri = oracle_code(name).nms_layered(O.quantize(L, 2.0, 31), 10, early_exit=True)
+            assert np.array_equal(o[0].cpu().numpy(), rb) and np.array_equal(o[1].cpu().numpy(), ri)
+            assert np.array_equal(o[2].cpu().numpy().astype(np.int32), ra)
