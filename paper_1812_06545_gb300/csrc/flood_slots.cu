@@ -65,25 +65,25 @@ struct FloodMultiArgs {
     float X;
 };
 
-// The check-node phase of one thread for codes of row degree <= 8: row r of every block row,
-// one loop per degree over the rows of that degree (exact bodies, no per-row dispatch; the
-// branch above degree 8 serves wider instances).  Flooding checks are independent, so the
-// order of the rows changes no result.
+// The check-node phase of one thread for codes of row degree <= 8: row r of every W-th block
+// row from w0 (in degree order), one loop per degree over the rows of that degree (exact
+// bodies, no per-row dispatch; the branch above degree 8 serves wider instances).  Flooding
+// checks are independent, so the order of the rows changes no result.
 template <int D, int DMAX, int V, typename MsgT>
 __device__ __forceinline__ void cn_rows(const int32_t *t_rord, const int32_t *t_dbeg, const int32_t *t_rowptr,
                                         const int4 *__restrict__ t_ed, const char *Ar, char *Rr, int r, int ZA,
-                                        int ZR, float X, float Xb, uint32_t (&pbad)[V])
+                                        int ZR, float X, float Xb, uint32_t (&pbad)[V], int w0, int W)
 {
     if constexpr (D <= 8) {
         if constexpr (D <= DMAX) {
             const int i1 = t_dbeg[D - 1];
-            for (int i = t_dbeg[D - 2]; i < i1; i++)
+            for (int i = t_dbeg[D - 2] + w0; i < i1; i += W)
                 slot_check_v<D, true, V, MsgT>(D, t_ed + t_rowptr[t_rord[i]], Ar, Rr, r, ZA, ZR, X, Xb, pbad);
         }
-        cn_rows<D + 1, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+        cn_rows<D + 1, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad, w0, W);
     } else if constexpr (DMAX > 8) {
         const int i1 = t_dbeg[8];
-        for (int i = t_dbeg[7]; i < i1; i++) {
+        for (int i = t_dbeg[7] + w0; i < i1; i += W) {
             const int l = t_rord[i], b0 = t_rowptr[l];
             slot_check_dispatch<12, DMAX, V, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
         }
@@ -125,7 +125,7 @@ __device__ __forceinline__ void vn_column(int dv, const int32_t *__restrict__ ce
 // Barrier groups of a CTA: named barriers 1..15 (barrier 0 is the CTA's).
 constexpr int FLOOD_GROUPS_MAX = 15;
 
-template <int DMAX, int V, typename MsgT>
+template <int DMAX, int V, typename MsgT, bool SPREAD>
 __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const __grid_constant__ FloodMultiArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -182,9 +182,14 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
         // whole CTA: thread tid owns row tid mod Z of thread slot tid / Z.
         const int K = V == 2 ? gd.K : G, TPG = V == 2 ? gd.TPG : nth;
         const int bg = V == 2 ? tid / TPG : 0, u = V == 2 ? tid - bg * TPG : tid;
-        const int g = bg * K + u / Z, r = u - (u / Z) * Z;
+        // single slots spread over W groups of Z threads: thread u is group w0 = (u / Z) mod W
+        // of slot (u / Z) / W and works on block rows and columns w0, w0 + W, ... at position r
+        const int W = SPREAD ? gd.W : 1;  // a compile-time 1 unless spread (no loop strides to pay)
+        const int g = bg * K + (SPREAD ? u / (Z * W) : u / Z), r = u - (u / Z) * Z;
+        const int w0 = SPREAD ? (u / Z) % W : 0;
         const bool mine = g < G && (V == 1 || u < K * Z);
         const bool member = bg * K < G;  // the group has slots (else whole idle warps)
+        const bool lead = r == 0 && w0 == 0;  // the thread that takes codewords for the slot
 
         // a slot's leader takes the group's next codeword and finds its request
         auto grab = [&](int s) {
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
             fresh[s] = loc;
             sreq[s] = rq;
         };
-        if (mine && r == 0) {
+        if (mine && lead) {
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 grab(g * V + v);
@@ -227,19 +232,19 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
         auto refill = [&](int v) {
             const float *Lr = static_cast<const float *>(a.d.reqs[rq[v]].llr) + cw[v] * N;
             constexpr int CH = (V == 1 && DMAX <= 8) ? LDPC_REFILL_CHUNK_NARROW : LDPC_REFILL_CHUNK;
-            for (int j0 = 0; j0 < nb; j0 += CH) {
+            for (int j0 = w0; j0 < nb; j0 += CH * W) {
                 float x[CH];
 #pragma unroll
                 for (int u = 0; u < CH; u++)
-                    if (j0 + u < nb) x[u] = __ldg(Lr + (j0 + u) * Z + r);
+                    if (j0 + u * W < nb) x[u] = __ldg(Lr + (j0 + u * W) * Z + r);
 #pragma unroll
                 for (int u = 0; u < CH; u++)
-                    if (j0 + u < nb) {
+                    if (j0 + u * W < nb) {
                         if (!isfinite(x[u])) atomicOr(cd->status, IN_NONFINITE);
-                        A[((j0 + u) * Z + r) * V + v] = x[u] + 0.0f;
+                        A[((j0 + u * W) * Z + r) * V + v] = x[u] + 0.0f;
                     }
             }
-            for (int b = 0; b < nnz; b++) {
+            for (int b = w0; b < nnz; b += W) {
                 if constexpr (sizeof(MsgT) == 2)
                     Rc[(b * Z + r) * V + v] = __float2half_rn(0.0f);
                 else
@@ -288,11 +293,11 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
 #pragma unroll
                 for (int v = 0; v < V; v++) pbad[v] = 0;
                 if constexpr (DMAX == 8) {
-                    cn_rows<2, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+                    cn_rows<2, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad, w0, W);
                 } else {
                     // codes with rows above degree 8: per-row dispatch in row order (measured
                     // faster here than the per-degree loops on the mixed-code launch)
-                    for (int l = 0; l < mb; l++) {
+                    for (int l = w0; l < mb; l += W) {
                         const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
                         slot_check_dispatch<2, DMAX, V, MsgT>(dc, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
                     }
@@ -315,18 +320,18 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                 anyact |= act[v];
             }
             if (anyact) {
-                for (int j0 = 0; j0 < nb; j0 += 4) {
+                for (int j0 = w0; j0 < nb; j0 += 4 * W) {
                     float lv[4][V];
 #pragma unroll
                     for (int u = 0; u < 4; u++)
 #pragma unroll
                         for (int v = 0; v < V; v++)
-                            if (j0 + u < nb && act[v])
+                            if (j0 + u * W < nb && act[v])
                                 lv[u][v] = __ldg(static_cast<const float *>(a.d.reqs[rq[v]].llr) + cw[v] * N +
-                                                 (j0 + u) * Z + r);
+                                                 (j0 + u * W) * Z + r);
 #pragma unroll
                     for (int u = 0; u < 4; u++) {
-                        const int j = j0 + u;
+                        const int j = j0 + u * W;
                         if (j < nb) {
                             float sacc[V];
 #pragma unroll
@@ -350,12 +355,12 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                     const ReqDev &q = a.d.reqs[rq[v]];
                     uint8_t *Bo = q.bits + cw[v] * N;
                     float *Ao = q.app ? q.app + cw[v] * N : nullptr;
-                    for (int j = 0; j < nb; j++) {
+                    for (int j = w0; j < nb; j += W) {
                         const float x = A[(j * Z + r) * V + v];
                         Bo[j * Z + r] = x < 0.0f ? 1 : 0;
                         if (Ao) Ao[j * Z + r] = x;
                     }
-                    if (r == 0) {
+                    if (lead) {
                         q.iters[cw[v]] = t[v];
                         grab(g * V + v);
                     }
@@ -368,7 +373,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
             if (mine) {
 #pragma unroll
                 for (int v = 0; v < V; v++) {
-                    if (r == 0) bad[g * V + v] = 0;
+                    if (lead) bad[g * V + v] = 0;
                     if (done[v]) {
                         cw[v] = fresh[g * V + v];
                         rq[v] = sreq[g * V + v];
@@ -463,20 +468,28 @@ static int choose_v(const CodeDev &h, int msg, int tbl_ints, size_t limit)
     return (c2 >= 2 && c2 >= c1) ? 2 : 1;
 }
 
-template <int DMAX, int V, typename MsgT>
+template <int DMAX, int V, typename MsgT, bool SPREAD = false>
 static cudaError_t launch_multi(const FloodMultiArgs &a, size_t smem, int threads, int ctas, cudaStream_t s)
 {
-    cudaError_t e = ensure_smem<k_flood_slots<DMAX, V, MsgT>>(smem);
+    cudaError_t e = ensure_smem<k_flood_slots<DMAX, V, MsgT, SPREAD>>(smem);
     if (e != cudaSuccess) return e;
     LaunchScope ls(F_SLOTS, s);
-    k_flood_slots<DMAX, V, MsgT><<<(unsigned)ctas, threads, smem, s>>>(a);
+    k_flood_slots<DMAX, V, MsgT, SPREAD><<<(unsigned)ctas, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+// spread: single slots of a small batch whose block rows and columns are spread over W > 1
+// thread groups (V = 1 only)
 template <typename MsgT>
-static cudaError_t launch_multi_d(int dmax, int V, const FloodMultiArgs &a, size_t smem, int threads, int ctas,
-                                  cudaStream_t s)
+static cudaError_t launch_multi_d(int dmax, int V, bool spread, const FloodMultiArgs &a, size_t smem, int threads,
+                                  int ctas, cudaStream_t s)
 {
+    if (spread) {
+        if (dmax <= 8) return launch_multi<8, 1, MsgT, true>(a, smem, threads, ctas, s);
+        if (dmax <= 16) return launch_multi<16, 1, MsgT, true>(a, smem, threads, ctas, s);
+        if (dmax <= 24) return launch_multi<24, 1, MsgT, true>(a, smem, threads, ctas, s);
+        return launch_multi<32, 1, MsgT, true>(a, smem, threads, ctas, s);
+    }
     if (dmax <= 8)
         return V == 2 ? launch_multi<8, 2, MsgT>(a, smem, threads, ctas, s)
                       : launch_multi<8, 1, MsgT>(a, smem, threads, ctas, s);
@@ -517,6 +530,17 @@ cudaError_t flood_multi_decode(const HostReq *reqs, int n, const ldpc_decode_par
     const int tuned = codes[0]->tuned_flood[p.msg == LDPC_MSG_F16 ? 1 : 0];
     int V = tuned == SCHED_SLOTS_V2 ? 2 : tuned == SCHED_SLOTS_V1 ? 1 : choose_v(codes[0]->host, p.msg, tbl, limit);
     if (!tuned && dmax > 16) V = 1;
+    // a small batch (every group's codewords per SM leave room to spread a single slot over at
+    // least two thread groups) decodes in single slots spread over the threads: lower latency
+    bool small = !tuned;
+    for (int g = 0; g < ng && small; g++) {
+        int64_t items = 0;
+        for (int i = 0; i < n; i++)
+            if (reqs[i].n_cw > 0 && reqs[i].code == codes[g]) items += reqs[i].n_cw;
+        const int64_t per_sm = (items + sm_count() - 1) / sm_count();
+        small = per_sm * 2 * codes[g]->host.Z <= slot_threads_max<1>() && codes[g]->host.mb >= 2;
+    }
+    if (small) V = 1;
     for (int g = 0; g < ng && V == 2; g++)
         if (slots_for(codes[g]->host, p.msg, 2, tbl, limit) < 2) V = 1;
     size_t smem = 0;
@@ -566,7 +590,16 @@ cudaError_t flood_multi_decode(const HostReq *reqs, int n, const ldpc_decode_par
         // groups need no more threads than one lock-step group of all of them (the idle lanes
         // of a group are only those of its last warp); one group when none does, and always
         // for single slots
-        const int G = gd.C / V, t0 = ((G * h.Z + 31) / 32) * 32;
+        const int G = gd.C / V;
+        // single slots of a small batch (slots capped below what the threads allow) spread each
+        // slot's block rows and columns over W groups of Z threads, up to the thread budget; other
+        // launches keep W = 1 and the kernel instance without the spread
+        gd.W = 1;
+        if (small) {
+            const int wmax = slot_threads_max<1>() / (G * h.Z);
+            gd.W = wmax < 1 ? 1 : (wmax > h.mb ? h.mb : wmax);
+        }
+        const int t0 = ((G * gd.W * h.Z + 31) / 32) * 32;
         gd.K = G;
         gd.TPG = t0;
         for (int k = 1; V == 2 && k < G; k++) {
@@ -598,8 +631,10 @@ cudaError_t flood_multi_decode(const HostReq *reqs, int n, const ldpc_decode_par
     if (min_ctas < ctas) ctas = (int)min_ctas;
     cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * ng, s);
     if (e != cudaSuccess) return e;
-    return p.msg == LDPC_MSG_F16 ? launch_multi_d<__half>(dmax, V, a, smem, threads, ctas, s)
-                                 : launch_multi_d<float>(dmax, V, a, smem, threads, ctas, s);
+    bool spread = false;
+    for (int g = 0; g < ng; g++) spread |= a.d.groups[g].W > 1;
+    return p.msg == LDPC_MSG_F16 ? launch_multi_d<__half>(dmax, V, spread, a, smem, threads, ctas, s)
+                                 : launch_multi_d<float>(dmax, V, spread, a, smem, threads, ctas, s);
 }
 
 }  // namespace ldpc

@@ -101,6 +101,10 @@ struct GroupDev {
     int N, E, Z, mb, nb, nnz, dc_max;
     int64_t n_items;
     float cumw;  // cumulative share of the launch's work (initial CTA placement)
+    // single slots: thread groups of Z threads a slot's block rows and columns are spread over
+    // (1 unless a small batch leaves threads to spare).  Kept last: the field ahead of the
+    // others changed the slot decoder's parameter loads and cost it 2-3 % (measured).
+    int W;
 };
 struct MultiDesc {
     int n_groups;
