@@ -1048,6 +1048,17 @@ def main():
                 "fer": float((bb.cpu().numpy() != bc).any(axis=1).mean()),
                 "edge_updates_per_s": bcode.E * float(bi.sum()) / (bms * 1e-3)}
         forms["large_code"] = large
+        # the autotuner's candidate times on the headline code (a separate code object, so no
+        # other section sees the pick): one or two codewords per thread in the slot decoder,
+        # or the streaming kernels, on the 1.0 dB batch of 8192 codewords
+        acode = ldpc.Code(B, Z)
+        tuned = {}
+        for form in ("flood_f32", "flood_f16"):
+            choice, tms = ldpc.ldpc_autotune(acode.handle, params(form), xs[0], ldpc.LDPC_LLR_F32, n_per_batch, stream)
+            tuned[form] = {"choice": {1: "slots x1", 2: "slots x2", 3: "streaming"}.get(choice, str(choice)),
+                           "ms_slots_x1": float(tms[0]), "ms_slots_x2": float(tms[1]), "ms_streaming": float(tms[2])}
+        forms["autotune_headline_code"] = tuned
+        del acode
         # int8 layered min-sum on its own workload (rate 5/6, 65536 codewords, 4.0 dB)
         lw, LB, LZ, lframes = workload_frames(LAYERED_WORKLOAD, rank)
         lcode = ldpc.Code(LB, LZ)
