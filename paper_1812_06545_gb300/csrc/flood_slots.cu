@@ -72,20 +72,20 @@ struct FloodMultiArgs {
 template <int D, int DMAX, int V, typename MsgT>
 __device__ __forceinline__ void cn_rows(const int32_t *t_rord, const int32_t *t_dbeg, const int32_t *t_rowptr,
                                         const int4 *__restrict__ t_ed, const char *Ar, char *Rr, int r, int ZA,
-                                        int ZR, float X, float Xb, uint32_t (&pbad)[V], int w0, int W)
+                                        int ZR, float X, float Xb, float Pb, uint32_t (&pbad)[V], int w0, int W)
 {
     if constexpr (D <= 8) {
         if constexpr (D <= DMAX) {
             const int i1 = t_dbeg[D - 1];
             for (int i = t_dbeg[D - 2] + w0; i < i1; i += W)
-                slot_check_v<D, true, V, MsgT>(D, t_ed + t_rowptr[t_rord[i]], Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+                slot_check_v<D, true, V, MsgT>(D, t_ed + t_rowptr[t_rord[i]], Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
         }
-        cn_rows<D + 1, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad, w0, W);
+        cn_rows<D + 1, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad, w0, W);
     } else if constexpr (DMAX > 8) {
         const int i1 = t_dbeg[8];
         for (int i = t_dbeg[7] + w0; i < i1; i += W) {
             const int l = t_rord[i], b0 = t_rowptr[l];
-            slot_check_dispatch<12, DMAX, V, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+            slot_check_dispatch<12, DMAX, V, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
         }
     }
 }
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
     float *APPs = reinterpret_cast<float *>(smem + slots_smem_head(a.tbl_ints));
 
     const int tid = threadIdx.x, nth = blockDim.x;
-    const float X = a.X, Xb = a.X * kSLog2e;
+    const float X = a.X, Xb = a.X * kSLog2e, Pb = s_psi_in<false>(a.X);  // X, X log2 e, phi(X) log2 e
     constexpr uint32_t kSign = 0x80000000u;
     int grp = 0;
     {
@@ -293,13 +293,13 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
 #pragma unroll
                 for (int v = 0; v < V; v++) pbad[v] = 0;
                 if constexpr (DMAX == 8) {
-                    cn_rows<2, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad, w0, W);
+                    cn_rows<2, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad, w0, W);
                 } else {
                     // codes with rows above degree 8: per-row dispatch in row order (measured
                     // faster here than the per-degree loops on the mixed-code launch)
                     for (int l = w0; l < mb; l += W) {
                         const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
-                        slot_check_dispatch<2, DMAX, V, MsgT>(dc, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+                        slot_check_dispatch<2, DMAX, V, MsgT>(dc, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
                     }
                 }
 #pragma unroll

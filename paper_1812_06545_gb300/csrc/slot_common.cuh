@@ -131,7 +131,7 @@ __device__ __forceinline__ T *at(char *base, int off) { return reinterpret_cast<
 
 template <int D, bool EXACT, int V, typename MsgT>
 __device__ __forceinline__ void slot_check(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr, int r,
-                                           int ZA, int ZR, float X, float Xb, uint32_t (&pbad)[V])
+                                           int ZA, int ZR, float X, float Xb, float Pb, uint32_t (&pbad)[V])
 {
     constexpr uint32_t kSign = 0x80000000u;
     float av[D][V];
@@ -270,7 +270,7 @@ __device__ __forceinline__ float2 phi_out2(float2 s2)
 
 template <int D, bool EXACT, typename MsgT>
 __device__ __forceinline__ void slot_check_pair(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr, int r,
-                                                int ZA, int ZR, float X, float Xb, uint32_t (&pbad)[2])
+                                                int ZA, int ZR, float X, float Xb, float Pb, uint32_t (&pbad)[2])
 {
     constexpr uint32_t kSign = 0x80000000u;
     float2 av[D];
@@ -349,35 +349,208 @@ __device__ __forceinline__ void slot_check_pair(int dc, const int4 *__restrict__
     pbad[1] |= par1;
 }
 
+// The same check rule in the product (tanh) domain, rows of degree <= 8.  With
+// d_j = e^-a_j (a_j = min(|Q_j|, X)), tanh(a_j / 2) = (1 - d_j) / (1 + d_j); the exclusive
+// product P_k of the other edges' tanh gives R_k = ln((1 + P_k) / (1 - P_k)), which equals
+// phi(sum_{j != k} phi(a_j)) exactly (phi(x) = -ln tanh(x / 2) is its own inverse).
+// With B = prod (1 + d_j) and A = prod (1 - d_j), the pair alpha = (B + A) / 2,
+// beta = (B - A) / 2 gives (1 + P) / (1 - P) = alpha / beta, and one more factor d maps it
+// to (alpha + d beta, beta + d alpha): every term is non-negative, so neither 1 - P nor the
+// exclusion of edge k cancels (prefix and suffix pairs are combined as the product of the
+// two maps).  Per edge this is one ex2 and two lg2, against two of each phi evaluation
+// above, and no series branch.  The clamp of a_j to [phi(X), X] is a clamp of the ex2
+// argument to [-Xb, -Pb] (Xb = X log2 e, Pb = phi(X) log2 e).
+__device__ __forceinline__ void tanh_combine(float pa, float pb, float sa, float sb, float &al, float &be)
+{
+    al = fmaf(pb, sb, pa * sa);
+    be = fmaf(pb, sa, pa * sb);
+}
+
+template <int D, bool EXACT, typename MsgT>
+__device__ __forceinline__ void slot_check_tanh(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr, int r,
+                                                int ZA, int ZR, float Xb, float Pb, uint32_t (&pbad)[1])
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    float d[D];
+    uint32_t qs[D];
+    int xo[D];
+    uint32_t sg = 0, par = 0;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        d[k] = 0.0f;  // a missing edge (k >= dc) is the identity map
+        qs[k] = 0;
+        xo[k] = 0;
+        if (EXACT || k < dc) {
+            const EdgeRef e = edge_ref(ed[k], r, ZA, ZR);
+            xo[k] = e.orr;
+            float ap[1], rv[1];
+            SMsg<float, 1>::ld(at<float>(Ar, e.oa), ap);
+            SMsg<MsgT, 1>::ld(at<MsgT>(Rr, e.orr), rv);
+            const float q = ap[0] - rv[0];
+            par ^= __float_as_uint(ap[0]);
+            qs[k] = __float_as_uint(q) & kSign;
+            sg ^= qs[k];
+            d[k] = s_ex2(fminf(fmaxf(fabsf(q) * -kSLog2e, -Xb), -Pb));
+        }
+    }
+    // suffix maps of edges k..D-1 applied to (1, 0)
+    float sa[D + 1], sb[D + 1];
+    sa[D] = 1.0f;
+    sb[D] = 0.0f;
+    sa[D - 1] = 1.0f;
+    sb[D - 1] = d[D - 1];
+#pragma unroll
+    for (int k = D - 2; k >= 1; k--) {
+        sa[k] = fmaf(d[k], sb[k + 1], sa[k + 1]);
+        sb[k] = fmaf(d[k], sa[k + 1], sb[k + 1]);
+    }
+    float pa = 1.0f, pb = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        float al, be;
+        if (k == 0) {
+            al = sa[1];
+            be = sb[1];
+        } else if (k == D - 1) {
+            al = pa;
+            be = pb;
+        } else {
+            tanh_combine(pa, pb, sa[k + 1], sb[k + 1], al, be);
+        }
+        if (EXACT || k < dc) {
+            const float mag = fminf(s_lg2(al) - s_lg2(be), Xb) * kSLn2;
+            float out[1] = {__uint_as_float(__float_as_uint(mag) | (qs[k] ^ sg))};
+            SMsg<MsgT, 1>::st(at<MsgT>(Rr, xo[k]), out);
+        }
+        if (k == 0) {
+            pb = d[0];
+        } else if (k < D - 1) {
+            const float t = fmaf(d[k], pb, pa);
+            pb = fmaf(d[k], pa, pb);
+            pa = t;
+        }
+    }
+    pbad[0] |= par;
+}
+
+// Two codewords per thread: the maps' multiplies and FMAs issue as packed pairs.
+__device__ __forceinline__ void tanh_combine2(float2 pa, float2 pb, float2 sa, float2 sb, float2 &al, float2 &be)
+{
+    al = __ffma2_rn(pb, sb, __fmul2_rn(pa, sa));
+    be = __ffma2_rn(pb, sa, __fmul2_rn(pa, sb));
+}
+
+template <int D, bool EXACT, typename MsgT>
+__device__ __forceinline__ void slot_check_tanh_pair(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr,
+                                                     int r, int ZA, int ZR, float Xb, float Pb,
+                                                     uint32_t (&pbad)[2])
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    float2 d[D];
+    uint32_t qs0[D], qs1[D];
+    int xo[D];
+    uint32_t sg0 = 0, sg1 = 0, par0 = 0, par1 = 0;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        d[k] = f2(0.0f, 0.0f);
+        qs0[k] = qs1[k] = 0;
+        xo[k] = 0;
+        if (EXACT || k < dc) {
+            const EdgeRef e = edge_ref(ed[k], r, ZA, ZR);
+            xo[k] = e.orr;
+            float ap[2], rv[2];
+            SMsg<float, 2>::ld(at<float>(Ar, e.oa), ap);
+            SMsg<MsgT, 2>::ld(at<MsgT>(Rr, e.orr), rv);
+            const float2 q = __ffma2_rn(f2(rv[0], rv[1]), f2(-1.0f, -1.0f), f2(ap[0], ap[1]));
+            par0 ^= __float_as_uint(ap[0]);
+            par1 ^= __float_as_uint(ap[1]);
+            qs0[k] = __float_as_uint(q.x) & kSign;
+            qs1[k] = __float_as_uint(q.y) & kSign;
+            sg0 ^= qs0[k];
+            sg1 ^= qs1[k];
+            d[k] = f2(s_ex2(fminf(fmaxf(fabsf(q.x) * -kSLog2e, -Xb), -Pb)),
+                      s_ex2(fminf(fmaxf(fabsf(q.y) * -kSLog2e, -Xb), -Pb)));
+        }
+    }
+    float2 sa[D + 1], sb[D + 1];
+    sa[D] = f2(1.0f, 1.0f);
+    sb[D] = f2(0.0f, 0.0f);
+    sa[D - 1] = f2(1.0f, 1.0f);
+    sb[D - 1] = d[D - 1];
+#pragma unroll
+    for (int k = D - 2; k >= 1; k--) {
+        sa[k] = __ffma2_rn(d[k], sb[k + 1], sa[k + 1]);
+        sb[k] = __ffma2_rn(d[k], sa[k + 1], sb[k + 1]);
+    }
+    float2 pa = f2(1.0f, 1.0f), pb = f2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        float2 al, be;
+        if (k == 0) {
+            al = sa[1];
+            be = sb[1];
+        } else if (k == D - 1) {
+            al = pa;
+            be = pb;
+        } else {
+            tanh_combine2(pa, pb, sa[k + 1], sb[k + 1], al, be);
+        }
+        if (EXACT || k < dc) {
+            const float2 l = __fadd2_rn(f2(s_lg2(al.x), s_lg2(al.y)), f2(-s_lg2(be.x), -s_lg2(be.y)));
+            const float2 mag = __fmul2_rn(f2(fminf(l.x, Xb), fminf(l.y, Xb)), f2(kSLn2, kSLn2));
+            float out[2] = {__uint_as_float(__float_as_uint(mag.x) | (qs0[k] ^ sg0)),
+                            __uint_as_float(__float_as_uint(mag.y) | (qs1[k] ^ sg1))};
+            SMsg<MsgT, 2>::st(at<MsgT>(Rr, xo[k]), out);
+        }
+        if (k == 0) {
+            pb = d[0];
+        } else if (k < D - 1) {
+            const float2 t = __ffma2_rn(d[k], pb, pa);
+            pb = __ffma2_rn(d[k], pa, pb);
+            pa = t;
+        }
+    }
+    pbad[0] |= par0;
+    pbad[1] |= par1;
+}
+
+#ifndef LDPC_SLOTS_TANH
+#define LDPC_SLOTS_TANH 1  // product-domain check rule for rows of degree <= 8
+#endif
+
 #ifndef LDPC_SLOTS_PAIRED_FP
 #define LDPC_SLOTS_PAIRED_FP 1  // packed FP32x2 arithmetic for two codewords per thread
 #endif
 template <int D, bool EXACT, int V, typename MsgT>
 __device__ __forceinline__ void slot_check_v(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr, int r,
-                                             int ZA, int ZR, float X, float Xb, uint32_t (&pbad)[V])
+                                             int ZA, int ZR, float X, float Xb, float Pb, uint32_t (&pbad)[V])
 {
-    if constexpr (V == 2 && LDPC_SLOTS_PAIRED_FP)
-        slot_check_pair<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+    if constexpr (LDPC_SLOTS_TANH && D <= 8 && V == 1)
+        slot_check_tanh<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
+    else if constexpr (LDPC_SLOTS_TANH && D <= 8 && V == 2 && LDPC_SLOTS_PAIRED_FP)
+        slot_check_tanh_pair<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
+    else if constexpr (V == 2 && LDPC_SLOTS_PAIRED_FP)
+        slot_check_pair<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
     else
-        slot_check<D, EXACT, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+        slot_check<D, EXACT, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
 }
 
 template <int D, int DMAX, int V, typename MsgT>
 __device__ __forceinline__ void slot_check_dispatch(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr,
-                                                    int r, int ZA, int ZR, float X, float Xb, uint32_t (&pbad)[V])
+                                                    int r, int ZA, int ZR, float X, float Xb, float Pb, uint32_t (&pbad)[V])
 {
     if constexpr (D >= DMAX) {
-        slot_check_v<DMAX, false, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+        slot_check_v<DMAX, false, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
     } else if constexpr (D <= 8) {
         if (dc == D)
-            slot_check_v<D, true, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+            slot_check_v<D, true, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
         else
-            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
     } else {
         if (dc <= D)
-            slot_check_v<D, false, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+            slot_check_v<D, false, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
         else
-            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, pbad);
+            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
     }
 }
 

@@ -44,12 +44,12 @@ def oracle_code(name):
 F16_CASCADE_FRAC = 0.02
 
 
-def binary16_band(oc, layered: bool, L, T: int, mult: float):
-    """(ref, band): the FP64 oracle with binary16 message storage after T iterations (no
-    early exit) and the per-element band FP32_TOL * max(1, |ref|) + mult half-ulps of the sum
-    of the incoming message magnitudes."""
+def binary16_band(oc, layered: bool, L, T: int, mult: float, X: float = 80.0):
+    """(ref, band): the FP64 oracle (clamp X) with binary16 message storage after T
+    iterations (no early exit) and the per-element band FP32_TOL * max(1, |ref|) + mult
+    half-ulps of the sum of the incoming message magnitudes."""
     orc = oc.spa_layered if layered else oc.spa_flood
-    ref, _, _, R = orc(L, T, early_exit=False, fp16_msgs=True, return_messages=True)
+    ref, _, _, R = orc(L, T, early_exit=False, X=X, fp16_msgs=True, return_messages=True)
     band = FP32_TOL * np.maximum(1.0, np.abs(ref)) + mult * 2.0 ** -11 * oc.incoming_message_sum(R)
     return ref, band
 

@@ -66,6 +66,27 @@ def test_fp16_messages_first_three_iterations(cuda_dev, form, name, n, eb):
         assert_binary16_close(app, ref, band, strict=T == 1, what=(name, T))
 
 
+@pytest.mark.parametrize("form", ["flood_f32", "flood_f16", "stream_f32", "layered_f32"])
+@pytest.mark.parametrize("name,n,eb", [("qc12x24_z81_s2", 400, 2.0), ("qc8x24_z54_s45", 300, 2.5)])
+@pytest.mark.parametrize("X", [2.5, 6.0])
+def test_small_phi_clamp(cuda_dev, form, name, n, eb, X):
+    # a clamp X whose lower end phi(X) is far from 0 (phi(2.5) = 0.165, phi(6) = 0.005):
+    # both ends of [phi(X), X] bind on many messages, so a decoder that drops either end
+    # of the clamp, or applies it to the wrong quantity, leaves the tolerance
+    _, _, c, L = I.make_frames(name, n, eb, 91, 92)
+    oc = oracle_code(name)
+    for T in (1, 2, 3):
+        app, _, _ = run(name, form, L, cuda_dev, max_iter=T, early_exit=0, phi_clamp=X)
+        if form.endswith("f16"):
+            ref, band = binary16_band(oc, False, L, T, 4, X=X)
+            assert_binary16_close(app, ref, band, strict=T == 1, what=(name, T, X))
+            continue
+        orc = oc.spa_layered if form.startswith("layered") else oc.spa_flood
+        ref, _, _ = orc(L, T, early_exit=False, X=X)
+        err = rel_err(app, ref)
+        assert err.max() <= FP32_TOL, (form, name, T, X, err.max())
+
+
 @pytest.mark.parametrize("form", ["flood_f32", "stream_f32", "plain_f32", "layered_f32"])
 def test_erased_inputs(cuda_dev, form):
     # 10 % of the LLRs erased (exactly 0, some of them -0.0): a zero |Q| is clamped up to
