@@ -77,12 +77,81 @@ __host__ __device__ inline int cl_owner(const int *split, int x)
     return q;
 }
 
+#ifndef LDPC_CL_TANH
+#define LDPC_CL_TANH 1  // product-domain check rule for rows of degree <= 8
+#endif
+
+// An owned row of degree <= 8 in the product (tanh) domain (see slot_common.cuh): d_k = e^-a_k
+// with a_k = |Q_k| clamped to [phi(X), X], the other edges' maps combined from prefix and
+// suffix pairs, R_k = ln(alpha / beta); one ex2 and two lg2 per edge.
+template <int D, bool EXACT, typename MsgT>
+__device__ __forceinline__ uint32_t cl_check_tanh(int dc, const int4 *__restrict__ ed, MsgT *Rr, uint32_t app_0,
+                                                  uint32_t app_1, int r, int Z, float Xb, float Pb)
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    float d[D];
+    uint32_t qs[D];
+    uint32_t sg = 0, par = 0;
+    const uint32_t rb = 4u * (uint32_t)r, ZA = 4u * (uint32_t)Z;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        d[k] = 0.0f;  // a missing edge (k >= dc) is the identity map
+        qs[k] = 0;
+        if (EXACT || k < dc) {
+            const int4 e = ed[k];
+            const float ap = cl_ld((const float *)nullptr, (e.z ? app_1 : app_0) + e.x + rb - (r >= e.y ? ZA : 0u));
+            const float qv = ap - (float)Rr[k * Z];
+            par ^= __float_as_uint(ap);
+            qs[k] = __float_as_uint(qv) & kSign;
+            sg ^= qs[k];
+            d[k] = s_ex2(fminf(fmaxf(fabsf(qv) * -kSLog2e, -Xb), -Pb));
+        }
+    }
+    float sa[D + 1], sb[D + 1];
+    sa[D] = 1.0f;
+    sb[D] = 0.0f;
+    sa[D - 1] = 1.0f;
+    sb[D - 1] = d[D - 1];
+#pragma unroll
+    for (int k = D - 2; k >= 1; k--) {
+        sa[k] = fmaf(d[k], sb[k + 1], sa[k + 1]);
+        sb[k] = fmaf(d[k], sa[k + 1], sb[k + 1]);
+    }
+    float pa = 1.0f, pb = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        float al, be;
+        if (k == 0) {
+            al = sa[1];
+            be = sb[1];
+        } else if (k == D - 1) {
+            al = pa;
+            be = pb;
+        } else {
+            tanh_combine(pa, pb, sa[k + 1], sb[k + 1], al, be);
+        }
+        if (EXACT || k < dc) {
+            const float mag = fminf(s_lg2(al) - s_lg2(be), Xb) * kSLn2;
+            Rr[k * Z] = MsgT(__uint_as_float(__float_as_uint(mag) | (qs[k] ^ sg)));
+        }
+        if (k == 0) {
+            pb = d[0];
+        } else if (k < D - 1) {
+            const float t = fmaf(d[k], pb, pa);
+            pb = fmaf(d[k], pa, pb);
+            pa = t;
+        }
+    }
+    return par;
+}
+
 // One check of an owned row: Q = APP - R over its edges (posteriors wherever they live), the
 // phi rule, messages written in place; returns the parity of the posteriors' sign bits.
 template <int D, bool EXACT, typename MsgT>
 __device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed, MsgT *Rr, uint32_t app_0,
-                                             uint32_t app_1, int r, int Z, float X, float Xb)
+                                             uint32_t app_1, int r, int Z, float X, float Xb, float Pb)
 {
+    if constexpr (LDPC_CL_TANH && D <= 8) return cl_check_tanh<D, EXACT, MsgT>(dc, ed, Rr, app_0, app_1, r, Z, Xb, Pb);
     constexpr uint32_t kSign = 0x80000000u;
     float av[D];
     uint32_t sg = 0, par = 0;
@@ -143,16 +212,16 @@ __device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed
 template <int D, int DMAX, typename MsgT>
 __device__ __forceinline__ uint32_t cl_check_dispatch(int dc, const int4 *__restrict__ ent, MsgT *Rr,
                                                       uint32_t app_0, uint32_t app_1, int r, int Z, float X,
-                                                      float Xb)
+                                                      float Xb, float Pb)
 {
     if constexpr (D >= DMAX) {
-        return cl_check<DMAX, false, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
+        return cl_check<DMAX, false, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb, Pb);
     } else if constexpr (D <= 8) {
-        if (dc == D) return cl_check<D, true, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
-        return cl_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
+        if (dc == D) return cl_check<D, true, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb, Pb);
+        return cl_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb, Pb);
     } else {
-        if (dc <= D) return cl_check<D, false, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
-        return cl_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb);
+        if (dc <= D) return cl_check<D, false, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb, Pb);
+        return cl_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb, Pb);
     }
 }
 
@@ -210,7 +279,7 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
     const int q = (int)cluster.block_rank();
     const int tid = threadIdx.x, nth = blockDim.x;
     const int Z = cd->Z, mb = cd->mb, nb = cd->nb, nnz = cd->nnz;
-    const float X = a.X, Xb = a.X * kSLog2e;
+    const float X = a.X, Xb = a.X * kSLog2e, Pb = s_psi_in<false>(a.X);  // X, X log2 e, phi(X) log2 e
 
     // bookkeeping: [0] bad flags (2, alternating by round), [2] the codeword being decoded
     // (int64 at 8: request << 32 | request-local index, -1 when the work is done)
@@ -310,7 +379,7 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
                 const int b0 = t_rowptr[l];
                 const uint32_t par = cl_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0,
                                                                       R + (b0 - blk0) * Z + r, app_0, app_1, r, Z,
-                                                                      X, Xb);
+                                                                      X, Xb, Pb);
                 pbad |= (par & kSign) != 0;
             };
             for (int r = p0; works && r < Z; r += ps)

@@ -87,12 +87,97 @@ struct MsgIO<__half> {
 // base (row r), with no wrap.
 __device__ __forceinline__ int lspa_app_off(const int4 d, int r, int ZA) { return d.x - (r >= d.z ? ZA : 0); }
 
+#ifndef LDPC_LSPA_TANH
+#define LDPC_LSPA_TANH 1  // product-domain check rule for rows of degree <= 8
+#endif
+
+// One check of row r (degree <= 8) in the product (tanh) domain: with d_k = e^-a_k,
+// a_k = |Q_k| clamped to [phi(X), X], the pair (alpha, beta) of the other edges' maps
+// (alpha, beta) <- (alpha + d beta, beta + d alpha) from (1, 0) gives
+// R'_k = ln(alpha / beta) = phi(sum_{other} phi(a)) (see slot_common.cuh); one ex2 and two
+// lg2 per edge.  In base-2 units (FP32 form) neither the ex2 argument nor the lg2
+// difference needs a scaling multiply.  The FP32 form holds Q per edge; the FP16 form
+// (1024 threads, 64 registers) forms it again from APP and R, neither of which is written
+// before its own edge is.
+template <int D, bool EXACT, typename MsgT>
+__device__ __forceinline__ void layer_check_tanh(int dc, const int4 *__restrict__ ed, char *Ar, char *Rr, int r, int ZA,
+                                                 float Xb, float Pb)
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    constexpr bool B2 = kBase2<MsgT>, kHoldQ = sizeof(MsgT) == 4;
+    MsgT *Rl = at<MsgT>(Rr, ed[0].y);
+    const int Zm = ZA / (int)sizeof(float);
+    float d[D];
+    int ao[D];
+    float q[kHoldQ ? D : 1];
+    uint32_t sg = 0;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        d[k] = 0.0f;  // a missing edge (k >= dc) is the identity map
+        ao[k] = 0;
+        if (EXACT || k < dc) {
+            ao[k] = lspa_app_off(ed[k], r, ZA);
+            const float qk = *at<float>(Ar, ao[k]) - MsgIO<MsgT>::ld(Rl + k * Zm);
+            if constexpr (kHoldQ) q[k] = qk;
+            sg ^= __float_as_uint(qk);
+            const float arg = B2 ? -fabsf(qk) : fabsf(qk) * -kSLog2e;
+            d[k] = s_ex2(fminf(fmaxf(arg, -Xb), -Pb));
+        }
+    }
+    float sa[D + 1], sb[D + 1];
+    sa[D] = 1.0f;
+    sb[D] = 0.0f;
+    sa[D - 1] = 1.0f;
+    sb[D - 1] = d[D - 1];
+#pragma unroll
+    for (int k = D - 2; k >= 1; k--) {
+        sa[k] = fmaf(d[k], sb[k + 1], sa[k + 1]);
+        sb[k] = fmaf(d[k], sa[k + 1], sb[k + 1]);
+    }
+    float pa = 1.0f, pb = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; k++) {
+        float al, be;
+        if (k == 0) {
+            al = sa[1];
+            be = sb[1];
+        } else if (k == D - 1) {
+            al = pa;
+            be = pb;
+        } else {
+            tanh_combine(pa, pb, sa[k + 1], sb[k + 1], al, be);
+        }
+        if (EXACT || k < dc) {
+            const float l = fminf(s_lg2(al) - s_lg2(be), Xb);
+            const float mag = B2 ? l : l * kSLn2;
+            float qk;
+            if constexpr (kHoldQ)
+                qk = q[k];
+            else
+                qk = *at<float>(Ar, ao[k]) - MsgIO<MsgT>::ld(Rl + k * Zm);
+            const float out = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(qk) ^ sg) & kSign));
+            *at<float>(Ar, ao[k]) = qk + MsgIO<MsgT>::st(Rl + k * Zm, out);
+        }
+        if (k == 0) {
+            pb = d[0];
+        } else if (k < D - 1) {
+            const float t = fmaf(d[k], pb, pa);
+            pb = fmaf(d[k], pa, pb);
+            pa = t;
+        }
+    }
+}
+
 // One check of row r in the layer whose blocks start at descriptor `ed`, computed from and
 // written back to the slot's APP (thread base Ar) and R (thread base Rr).
 template <int D, bool EXACT, typename MsgT>
 __device__ __forceinline__ void layer_check(int dc, const int4 *__restrict__ ed, char *Ar, char *Rr, int r, int ZA,
-                                            float X, float Xb)
+                                            float X, float Xb, float Pb)
 {
+    if constexpr (LDPC_LSPA_TANH && D <= 8) {
+        layer_check_tanh<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, Xb, Pb);
+        return;
+    }
     constexpr uint32_t kSign = 0x80000000u;
     // the layer's messages: row r of its blocks, one block (Z messages) apart
     MsgT *Rl = at<MsgT>(Rr, ed[0].y);
@@ -175,20 +260,20 @@ __device__ __forceinline__ void layer_check(int dc, const int4 *__restrict__ ed,
 
 template <int D, int DMAX, typename MsgT>
 __device__ __forceinline__ void layer_check_dispatch(int dc, const int4 *__restrict__ ed, char *Ar, char *Rr, int r,
-                                                     int ZA, float X, float Xb)
+                                                     int ZA, float X, float Xb, float Pb)
 {
     if constexpr (D >= DMAX) {
-        layer_check<DMAX, false, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb);
+        layer_check<DMAX, false, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb, Pb);
     } else if constexpr (D <= 8) {
         if (dc == D)
-            layer_check<D, true, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb);
+            layer_check<D, true, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb, Pb);
         else
-            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb);
+            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb, Pb);
     } else {
         if (dc <= D)
-            layer_check<D, false, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb);
+            layer_check<D, false, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb, Pb);
         else
-            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb);
+            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb, Pb);
     }
 }
 
@@ -261,6 +346,7 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
     const int tid = threadIdx.x, nth = blockDim.x;
     // clamp X in the internal units (base-2 for FP32 messages); phi values are base-2 units
     const float X = kBase2<MsgT> ? a.X * kSLog2e : a.X, Xb = a.X * kSLog2e;
+    const float Pb = s_psi_in<false>(a.X);  // phi(X) log2 e
     for (int i = tid; i < nnz; i += nth) {
         const int e = cd->ent[i], sh = e & 0xffff;
         t_ed[i] = make_int4((int)sizeof(float) * ((e >> 16) * Z + sh), (int)sizeof(MsgT) * i * Z, Z - sh, 0);
@@ -325,7 +411,7 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
         for (int l = 0; l < mb; l++) {
             if (busy) {
                 const int b0 = t_rowptr[l];
-                layer_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0, Ar, Rr, r, ZA, X, Xb);
+                layer_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0, Ar, Rr, r, ZA, X, Xb, Pb);
             }
             group_sync(g, TPG);
         }
