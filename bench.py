@@ -494,7 +494,7 @@ def summary_line(line: dict, details_path: str) -> dict:
     rf = line["roofline"]
     out["roofline"] = {"bound": rf["bound"], "kernel": "k_flood_slots", "achieved": rf["achieved"],
                        "peak": rf["peak"], "unit": rf["unit"], "frac": rf["frac"], "traffic": rf["traffic"],
-                       "peak_source": "SFU rates measured live: 1/(2/ex2+4/lg2) edge updates/s"}
+                       "peak_source": "SFU rates measured live: 1/(1/ex2+2/lg2) edge updates/s"}
     out["latency_ms"] = {"p50": line["latency_ms"]["p50"], "p99": line["latency_ms"]["p99"]}
     e2e = line["e2e"]
     out["e2e"] = {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "streams")}
@@ -919,14 +919,17 @@ def main():
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     N, E, T = code.N, code.E, w.max_iter
 
-    # roofline of the slot decoder (the headline form's only kernel): compute-bound; every
-    # edge update needs two phi evaluations, each an exponential and the logarithm of a
-    # ratio (a logarithm and a reciprocal, or two logarithms; rcp.approx runs at the lg2
-    # rate), on the special-function units whose throughput is measured live
+    # roofline of the slot decoder (the headline form's only kernel): compute-bound; in the
+    # product (tanh) domain every edge update needs one exponential (of |Q|) and the
+    # logarithm of one ratio (of the other edges' pair: two logarithms, or a logarithm and
+    # a reciprocal; rcp.approx runs at the lg2 rate), on the special-function units whose
+    # throughput is measured live.  The phi-domain rule (two phi per edge update, each an
+    # exponential and the logarithm of a ratio) has half this ceiling.
     n_sl, sl_ms = ldpc.ldpc_profile_read("slots")
     edge_updates = args.steps * E * int(sum(int(it.sum()) for it in iters_np))
     ex2_s, lg2_s = ldpc.ldpc_sfu_throughput(stream)
-    sfu_peak = 1.0 / (2.0 / ex2_s + 4.0 / lg2_s) / 1e9                  # Gedge/s
+    sfu_peak = 1.0 / (1.0 / ex2_s + 2.0 / lg2_s) / 1e9                  # Gedge/s
+    sfu_peak_phi = 1.0 / (2.0 / ex2_s + 4.0 / lg2_s) / 1e9
     achieved = edge_updates / (sl_ms * 1e-3) / 1e9 if sl_ms > 0 else None
     traffic = stored_traffic("k_flood_slots", SLOTS_SOURCES)
     roofline = {"bound": "alu", "kernel": "k_flood_slots (on-chip flooding slot decoder)", "achieved": achieved,
@@ -934,8 +937,9 @@ def main():
                 "peak_source": (f"derived from the special-function throughput measured live on this GPU "
                                 f"(ex2 {ex2_s / 1e12:.2f} T/s = {ex2_s / n_sm / (sm_mhz * 1e6):.1f}/clk/SM, lg2 "
                                 f"{lg2_s / 1e12:.2f} T/s = {lg2_s / n_sm / (sm_mhz * 1e6):.1f}/clk/SM at {sm_mhz:.0f} MHz): "
-                                f"1 / (2/ex2 + 4/lg2) edge updates per second, two phi per edge update, each an "
-                                f"exponential and the logarithm of a ratio (two lg2-rate operations)"),
+                                f"1 / (1/ex2 + 2/lg2) edge updates per second: the product-domain check rule, "
+                                f"one exponential and the logarithm of one ratio (two lg2-rate operations) per "
+                                f"edge update; the phi-domain rule's ceiling is {sfu_peak_phi:.1f}"),
                 "traffic": traffic, "launches": n_sl, "avg_launch_ms": sl_ms / max(n_sl, 1),
                 "algorithmic_work": "edge updates = E x iterations run, summed over codewords"}
     # the same throughput against the HBM limit of a flooding decoder that streams its state

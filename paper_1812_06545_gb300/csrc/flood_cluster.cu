@@ -152,6 +152,20 @@ __device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed
                                              uint32_t app_1, int r, int Z, float X, float Xb, float Pb)
 {
     if constexpr (LDPC_CL_TANH && D <= 8) return cl_check_tanh<D, EXACT, MsgT>(dc, ed, Rr, app_0, app_1, r, Z, Xb, Pb);
+    if constexpr (LDPC_CL_TANH && D > 8) {
+        // rows above degree 8: the grouped rule, Q formed from APP and R in both passes
+        uint32_t par = 0;
+        const uint32_t rb = 4u * (uint32_t)r, ZA = 4u * (uint32_t)Z;
+        auto qof = [&](int k, bool first) -> float {
+            const int4 e = ed[k];
+            const float ap = cl_ld((const float *)nullptr, (e.z ? app_1 : app_0) + e.x + rb - (r >= e.y ? ZA : 0u));
+            if (first) par ^= __float_as_uint(ap);
+            return ap - (float)Rr[k * Z];
+        };
+        auto put = [&](int k, float m, float) { Rr[k * Z] = MsgT(m); };
+        tanh_check_wide<D, false>(dc, Xb, Pb, qof, put);
+        return par;
+    }
     constexpr uint32_t kSign = 0x80000000u;
     float av[D];
     uint32_t sg = 0, par = 0;

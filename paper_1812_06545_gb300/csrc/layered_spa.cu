@@ -177,6 +177,19 @@ __device__ __forceinline__ void layer_check(int dc, const int4 *__restrict__ ed,
     if constexpr (LDPC_LSPA_TANH && D <= 8) {
         layer_check_tanh<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, Xb, Pb);
         return;
+    } else if constexpr (LDPC_LSPA_TANH && D > 8) {
+        // rows above degree 8: the grouped rule, Q formed from APP and R in both passes
+        // (neither is written before its own edge is), APP = Q + R' at the store
+        MsgT *Rl = at<MsgT>(Rr, ed[0].y);
+        const int Zm = ZA / (int)sizeof(float);
+        auto qof = [&](int k, bool) -> float {
+            return *at<float>(Ar, lspa_app_off(ed[k], r, ZA)) - MsgIO<MsgT>::ld(Rl + k * Zm);
+        };
+        auto put = [&](int k, float m, float q) {
+            *at<float>(Ar, lspa_app_off(ed[k], r, ZA)) = q + MsgIO<MsgT>::st(Rl + k * Zm, m);
+        };
+        tanh_check_wide<D, kBase2<MsgT>>(dc, Xb, Pb, qof, put);
+        return;
     }
     constexpr uint32_t kSign = 0x80000000u;
     // the layer's messages: row r of its blocks, one block (Z messages) apart

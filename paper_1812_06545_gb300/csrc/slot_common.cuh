@@ -514,8 +514,274 @@ __device__ __forceinline__ void slot_check_tanh_pair(int dc, const int4 *__restr
     pbad[1] |= par1;
 }
 
+// The product-domain rule for a row of degree dc <= D with D > 8, in groups of 8 edges,
+// holding no per-edge state between its two passes (the registers of D pairs would spill):
+//   pass 1 forms every d_k and each group's pair (the product of its edges' maps);
+//   pass 2, group by group, forms the group's d_k again, its suffix pairs, and a prefix
+//   that starts from the product of the other groups' pairs.
+// Every term stays non-negative, as in the prefix / suffix form of rows up to degree 8.
+// qof(k, first) returns Q_k of edge k (`first`: pass 1, where the caller also takes what it
+// needs once per edge); put(k, R, Q) writes the signed message R of edge k (Q: its Q_k).  B2: Q and R in
+// base-2 units (LLR x log2 e), else natural units.
+__device__ __forceinline__ void pair_mul(float a1, float b1, float a2, float b2, float &a, float &b)
+{
+    a = fmaf(b1, b2, a1 * a2);
+    b = fmaf(b1, a2, a1 * b2);
+}
+
+template <bool B2>
+__device__ __forceinline__ float tanh_d(float q, float Xb, float Pb)
+{
+    return s_ex2(fminf(fmaxf(B2 ? -fabsf(q) : fabsf(q) * -kSLog2e, -Xb), -Pb));
+}
+
+template <int D, bool B2, typename QF, typename PF>
+__device__ __forceinline__ void tanh_check_wide(int dc, float Xb, float Pb, QF qof, PF put)
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    constexpr int G = (D + 7) / 8;
+    float ga[G], gb[G];
+    uint32_t sg = 0;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        ga[g] = 1.0f;
+        gb[g] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 8 * g + i;
+            if (k < D && k < dc) {
+                const float q = qof(k, true);
+                sg ^= __float_as_uint(q);
+                const float d = tanh_d<B2>(q, Xb, Pb);
+                if (i == 0) {
+                    gb[g] = d;
+                } else {
+                    const float t = fmaf(d, gb[g], ga[g]);
+                    gb[g] = fmaf(d, ga[g], gb[g]);
+                    ga[g] = t;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        if (8 * g >= dc) break;
+        // the other groups' product
+        float pa = 1.0f, pb = 0.0f;
+        bool first = true;
+#pragma unroll
+        for (int h = 0; h < G; h++) {
+            if (h == g) continue;
+            if (first) {
+                pa = ga[h];
+                pb = gb[h];
+                first = false;
+            } else {
+                pair_mul(pa, pb, ga[h], gb[h], pa, pb);
+            }
+        }
+        float d[8];
+        uint32_t qb[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 8 * g + i;
+            d[i] = 0.0f;
+            qb[i] = 0;
+            if (k < D && k < dc) {
+                const float q = qof(k, false);
+                qb[i] = __float_as_uint(q);
+                d[i] = tanh_d<B2>(q, Xb, Pb);
+            }
+        }
+        float sa[9], sb[9];
+        sa[8] = 1.0f;
+        sb[8] = 0.0f;
+        sa[7] = 1.0f;
+        sb[7] = d[7];
+#pragma unroll
+        for (int i = 6; i >= 1; i--) {
+            sa[i] = fmaf(d[i], sb[i + 1], sa[i + 1]);
+            sb[i] = fmaf(d[i], sa[i + 1], sb[i + 1]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 8 * g + i;
+            float al, be;
+            if (i == 7)
+                al = pa, be = pb;
+            else
+                pair_mul(pa, pb, sa[i + 1], sb[i + 1], al, be);
+            if (k < D && k < dc) {
+                const float l = fminf(s_lg2(al) - s_lg2(be), Xb);
+                const float mag = B2 ? l : l * kSLn2;
+                put(k, __uint_as_float(__float_as_uint(mag) | ((qb[i] ^ sg) & kSign)), __uint_as_float(qb[i]));
+            }
+            if (i < 7) {
+                const float t = fmaf(d[i], pb, pa);
+                pb = fmaf(d[i], pa, pb);
+                pa = t;
+            }
+        }
+    }
+}
+
+// Flooding slot decoder, one codeword per thread, rows above degree 8.
+template <int D, typename MsgT>
+__device__ __forceinline__ void slot_check_tanh_wide(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr,
+                                                     int r, int ZA, int ZR, float Xb, float Pb, uint32_t (&pbad)[1])
+{
+    uint32_t par = 0;
+    auto qof = [&](int k, bool first) -> float {
+        const EdgeRef e = edge_ref(ed[k], r, ZA, ZR);
+        float ap[1], rv[1];
+        SMsg<float, 1>::ld(at<float>(Ar, e.oa), ap);
+        SMsg<MsgT, 1>::ld(at<MsgT>(Rr, e.orr), rv);
+        if (first) par ^= __float_as_uint(ap[0]);
+        return ap[0] - rv[0];
+    };
+    // the message offset is formed again at the store (holding it per edge costs D registers)
+    auto put = [&](int k, float m, float) {
+        const EdgeRef e = edge_ref(ed[k], r, ZA, ZR);
+        float out[1] = {m};
+        SMsg<MsgT, 1>::st(at<MsgT>(Rr, e.orr), out);
+    };
+    tanh_check_wide<D, false>(dc, Xb, Pb, qof, put);
+    pbad[0] |= par;
+}
+
+// The grouped rule for two codewords per thread: the maps' multiplies and FMAs as packed
+// pairs.  qof(k, first) returns both codewords' Q_k, put(k, R) writes both messages.
+__device__ __forceinline__ void pair_mul2(float2 a1, float2 b1, float2 a2, float2 b2, float2 &a, float2 &b)
+{
+    a = __ffma2_rn(b1, b2, __fmul2_rn(a1, a2));
+    b = __ffma2_rn(b1, a2, __fmul2_rn(a1, b2));
+}
+
+template <int D, typename QF, typename PF>
+__device__ __forceinline__ void tanh_check_wide2(int dc, float Xb, float Pb, QF qof, PF put)
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    constexpr int G = (D + 7) / 8;
+    float2 ga[G], gb[G];
+    uint32_t sg0 = 0, sg1 = 0;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        ga[g] = f2(1.0f, 1.0f);
+        gb[g] = f2(0.0f, 0.0f);
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 8 * g + i;
+            if (k < D && k < dc) {
+                const float2 q = qof(k, true);
+                sg0 ^= __float_as_uint(q.x);
+                sg1 ^= __float_as_uint(q.y);
+                const float2 d = f2(tanh_d<false>(q.x, Xb, Pb), tanh_d<false>(q.y, Xb, Pb));
+                if (i == 0) {
+                    gb[g] = d;
+                } else {
+                    const float2 t = __ffma2_rn(d, gb[g], ga[g]);
+                    gb[g] = __ffma2_rn(d, ga[g], gb[g]);
+                    ga[g] = t;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        if (8 * g >= dc) break;
+        float2 pa = f2(1.0f, 1.0f), pb = f2(0.0f, 0.0f);
+        bool first = true;
+#pragma unroll
+        for (int h = 0; h < G; h++) {
+            if (h == g) continue;
+            if (first) {
+                pa = ga[h];
+                pb = gb[h];
+                first = false;
+            } else {
+                pair_mul2(pa, pb, ga[h], gb[h], pa, pb);
+            }
+        }
+        float2 d[8];
+        uint32_t qb0[8], qb1[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 8 * g + i;
+            d[i] = f2(0.0f, 0.0f);
+            qb0[i] = qb1[i] = 0;
+            if (k < D && k < dc) {
+                const float2 q = qof(k, false);
+                qb0[i] = __float_as_uint(q.x);
+                qb1[i] = __float_as_uint(q.y);
+                d[i] = f2(tanh_d<false>(q.x, Xb, Pb), tanh_d<false>(q.y, Xb, Pb));
+            }
+        }
+        float2 sa[9], sb[9];
+        sa[8] = f2(1.0f, 1.0f);
+        sb[8] = f2(0.0f, 0.0f);
+        sa[7] = f2(1.0f, 1.0f);
+        sb[7] = d[7];
+#pragma unroll
+        for (int i = 6; i >= 1; i--) {
+            sa[i] = __ffma2_rn(d[i], sb[i + 1], sa[i + 1]);
+            sb[i] = __ffma2_rn(d[i], sa[i + 1], sb[i + 1]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 8 * g + i;
+            float2 al, be;
+            if (i == 7)
+                al = pa, be = pb;
+            else
+                pair_mul2(pa, pb, sa[i + 1], sb[i + 1], al, be);
+            if (k < D && k < dc) {
+                const float2 l = __fadd2_rn(f2(s_lg2(al.x), s_lg2(al.y)), f2(-s_lg2(be.x), -s_lg2(be.y)));
+                const float2 mag = __fmul2_rn(f2(fminf(l.x, Xb), fminf(l.y, Xb)), f2(kSLn2, kSLn2));
+                put(k, f2(__uint_as_float(__float_as_uint(mag.x) | ((qb0[i] ^ sg0) & kSign)),
+                          __uint_as_float(__float_as_uint(mag.y) | ((qb1[i] ^ sg1) & kSign))));
+            }
+            if (i < 7) {
+                const float2 t = __ffma2_rn(d[i], pb, pa);
+                pb = __ffma2_rn(d[i], pa, pb);
+                pa = t;
+            }
+        }
+    }
+}
+
+// Flooding slot decoder, two codewords per thread, rows above degree 8.
+template <int D, typename MsgT>
+__device__ __forceinline__ void slot_check_tanh_pair_wide(int dc, const int4 *__restrict__ ed, const char *Ar,
+                                                          char *Rr, int r, int ZA, int ZR, float Xb, float Pb,
+                                                          uint32_t (&pbad)[2])
+{
+    uint32_t par0 = 0, par1 = 0;
+    auto qof = [&](int k, bool first) -> float2 {
+        const EdgeRef e = edge_ref(ed[k], r, ZA, ZR);
+        float ap[2], rv[2];
+        SMsg<float, 2>::ld(at<float>(Ar, e.oa), ap);
+        SMsg<MsgT, 2>::ld(at<MsgT>(Rr, e.orr), rv);
+        if (first) {
+            par0 ^= __float_as_uint(ap[0]);
+            par1 ^= __float_as_uint(ap[1]);
+        }
+        return __ffma2_rn(f2(rv[0], rv[1]), f2(-1.0f, -1.0f), f2(ap[0], ap[1]));
+    };
+    auto put = [&](int k, float2 m) {
+        const EdgeRef e = edge_ref(ed[k], r, ZA, ZR);
+        float out[2] = {m.x, m.y};
+        SMsg<MsgT, 2>::st(at<MsgT>(Rr, e.orr), out);
+    };
+    tanh_check_wide2<D>(dc, Xb, Pb, qof, put);
+    pbad[0] |= par0;
+    pbad[1] |= par1;
+}
+
 #ifndef LDPC_SLOTS_TANH
 #define LDPC_SLOTS_TANH 1  // product-domain check rule for rows of degree <= 8
+#endif
+#ifndef LDPC_SLOTS_TANH_WIDE
+#define LDPC_SLOTS_TANH_WIDE 1  // and, in groups of 8 edges, for rows above degree 8
 #endif
 
 #ifndef LDPC_SLOTS_PAIRED_FP
@@ -527,6 +793,10 @@ __device__ __forceinline__ void slot_check_v(int dc, const int4 *__restrict__ ed
 {
     if constexpr (LDPC_SLOTS_TANH && D <= 8 && V == 1)
         slot_check_tanh<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
+    else if constexpr (LDPC_SLOTS_TANH_WIDE && D > 8 && V == 1)
+        slot_check_tanh_wide<D, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
+    else if constexpr (LDPC_SLOTS_TANH_WIDE && D > 8 && V == 2 && LDPC_SLOTS_PAIRED_FP)
+        slot_check_tanh_pair_wide<D, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
     else if constexpr (LDPC_SLOTS_TANH && D <= 8 && V == 2 && LDPC_SLOTS_PAIRED_FP)
         slot_check_tanh_pair<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
     else if constexpr (V == 2 && LDPC_SLOTS_PAIRED_FP)
