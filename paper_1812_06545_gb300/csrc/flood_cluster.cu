@@ -7,8 +7,8 @@
 // of its variables wherever they live (distributed shared memory of the cluster); a variable
 // of CTA q reads the messages of its edges wherever they live.  One round (Sec. II two-phase
 // message passing, Algorithm 1 loop order), each phase closed by a cluster barrier:
-//   check-node phase   every owned check: Q = APP - R, R' from the phi rule (the arithmetic
-//                      of the slot decoders), written in place; the parity of the APP sign
+//   check-node phase   every owned check: Q = APP - R, R' from the check rule in the product
+//                      (tanh) domain of the slot decoders, written in place; the parity of the APP sign
 //                      bits over the check flags an unsatisfied check of the previous
 //                      iteration's decisions
 //   decision           no CTA of the cluster flagged a check and >= 1 iteration done: the
@@ -77,10 +77,6 @@ __host__ __device__ inline int cl_owner(const int *split, int x)
     return q;
 }
 
-#ifndef LDPC_CL_TANH
-#define LDPC_CL_TANH 1  // product-domain check rule for rows of degree <= 8
-#endif
-
 // An owned row of degree <= 8 in the product (tanh) domain (see slot_common.cuh): d_k = e^-a_k
 // with a_k = |Q_k| clamped to [phi(X), X], the other edges' maps combined from prefix and
 // suffix pairs, R_k = ln(alpha / beta); one ex2 and two lg2 per edge.
@@ -104,7 +100,7 @@ __device__ __forceinline__ uint32_t cl_check_tanh(int dc, const int4 *__restrict
             par ^= __float_as_uint(ap);
             qs[k] = __float_as_uint(qv) & kSign;
             sg ^= qs[k];
-            d[k] = s_ex2(fminf(fmaxf(fabsf(qv) * -kSLog2e, -Xb), -Pb));
+            d[k] = tanh_d<false>(qv, Xb, Pb);
         }
     }
     float sa[D + 1], sb[D + 1];
@@ -131,8 +127,7 @@ __device__ __forceinline__ uint32_t cl_check_tanh(int dc, const int4 *__restrict
             tanh_combine(pa, pb, sa[k + 1], sb[k + 1], al, be);
         }
         if (EXACT || k < dc) {
-            const float mag = fminf(s_lg2(al) - s_lg2(be), Xb) * kSLn2;
-            Rr[k * Z] = MsgT(__uint_as_float(__float_as_uint(mag) | (qs[k] ^ sg)));
+            Rr[k * Z] = MsgT(__uint_as_float(__float_as_uint(tanh_mag<false>(al, be)) | (qs[k] ^ sg)));
         }
         if (k == 0) {
             pb = d[0];
@@ -146,14 +141,16 @@ __device__ __forceinline__ uint32_t cl_check_tanh(int dc, const int4 *__restrict
 }
 
 // One check of an owned row: Q = APP - R over its edges (posteriors wherever they live), the
-// phi rule, messages written in place; returns the parity of the posteriors' sign bits.
+// check rule in the product (tanh) domain (slot_common.cuh), messages written in place;
+// returns the parity of the posteriors' sign bits.  Rows above degree 8 take the grouped
+// form, with Q formed from APP and R in both passes.
 template <int D, bool EXACT, typename MsgT>
 __device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed, MsgT *Rr, uint32_t app_0,
-                                             uint32_t app_1, int r, int Z, float X, float Xb, float Pb)
+                                             uint32_t app_1, int r, int Z, float Xb, float Pb)
 {
-    if constexpr (LDPC_CL_TANH && D <= 8) return cl_check_tanh<D, EXACT, MsgT>(dc, ed, Rr, app_0, app_1, r, Z, Xb, Pb);
-    if constexpr (LDPC_CL_TANH && D > 8) {
-        // rows above degree 8: the grouped rule, Q formed from APP and R in both passes
+    if constexpr (D <= 8) {
+        return cl_check_tanh<D, EXACT, MsgT>(dc, ed, Rr, app_0, app_1, r, Z, Xb, Pb);
+    } else {
         uint32_t par = 0;
         const uint32_t rb = 4u * (uint32_t)r, ZA = 4u * (uint32_t)Z;
         auto qof = [&](int k, bool first) -> float {
@@ -166,76 +163,21 @@ __device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed
         tanh_check_wide<D, false>(dc, Xb, Pb, qof, put);
         return par;
     }
-    constexpr uint32_t kSign = 0x80000000u;
-    float av[D];
-    uint32_t sg = 0, par = 0;
-    const uint32_t rb = 4u * (uint32_t)r, ZA = 4u * (uint32_t)Z;
-#pragma unroll
-    for (int k = 0; k < D; k++) {
-        if (EXACT || k < dc) {
-            const int4 d = ed[k];
-            const float ap = cl_ld((const float *)nullptr, (d.z ? app_1 : app_0) + d.x + rb - (r >= d.y ? ZA : 0u));
-            const float qv = ap - (float)Rr[k * Z];
-            par ^= __float_as_uint(ap);
-            const uint32_t qs = __float_as_uint(qv) & kSign;
-            sg ^= qs;
-            av[k] = __uint_as_float(__float_as_uint(fminf(s_psi_in<false>(fminf(fabsf(qv), X)), Xb)) | qs);
-        }
-    }
-    if constexpr (D <= 8) {
-        // exclusive sums from suffix and prefix sums (no cancellation)
-        float sf[D + 1];
-        sf[D] = 0.0f;
-#pragma unroll
-        for (int k = D - 1; k >= 0; k--) sf[k] = (EXACT || k < dc) ? sf[k + 1] + fabsf(av[k]) : 0.0f;
-        float pre = 0.0f;
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            if (EXACT || k < dc) {
-                const float mag = fminf(s_phi_out<false>(pre + sf[k + 1]), X);
-                pre += fabsf(av[k]);
-                Rr[k * Z] = MsgT(__uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k]) ^ sg) & kSign)));
-            }
-        }
-    } else {
-        // S - a_k, the dominant edge's sum formed directly
-        float S = 0.0f, amax = 0.0f;
-#pragma unroll
-        for (int k = 0; k < D; k++)
-            if (EXACT || k < dc) {
-                S += fabsf(av[k]);
-                amax = fmaxf(amax, fabsf(av[k]));
-            }
-        float o = 0.0f;
-#pragma unroll
-        for (int k = 0; k < D; k++)
-            if (EXACT || k < dc) o += (fabsf(av[k]) == amax) ? 0.0f : fabsf(av[k]);
-        const float sx = (amax > 0.5f * S) ? o : S - amax;
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            if (EXACT || k < dc) {
-                const float ak = fabsf(av[k]);
-                const float mag = fminf(s_phi_out<false>(ak == amax ? sx : S - ak), X);
-                Rr[k * Z] = MsgT(__uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k]) ^ sg) & kSign)));
-            }
-        }
-    }
-    return par;
 }
 
 template <int D, int DMAX, typename MsgT>
 __device__ __forceinline__ uint32_t cl_check_dispatch(int dc, const int4 *__restrict__ ent, MsgT *Rr,
-                                                      uint32_t app_0, uint32_t app_1, int r, int Z, float X,
-                                                      float Xb, float Pb)
+                                                      uint32_t app_0, uint32_t app_1, int r, int Z, float Xb,
+                                                      float Pb)
 {
     if constexpr (D >= DMAX) {
-        return cl_check<DMAX, false, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb, Pb);
+        return cl_check<DMAX, false, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, Xb, Pb);
     } else if constexpr (D <= 8) {
-        if (dc == D) return cl_check<D, true, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb, Pb);
-        return cl_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb, Pb);
+        if (dc == D) return cl_check<D, true, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, Xb, Pb);
+        return cl_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, Xb, Pb);
     } else {
-        if (dc <= D) return cl_check<D, false, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb, Pb);
-        return cl_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, X, Xb, Pb);
+        if (dc <= D) return cl_check<D, false, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, Xb, Pb);
+        return cl_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ent, Rr, app_0, app_1, r, Z, Xb, Pb);
     }
 }
 
@@ -293,7 +235,7 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
     const int q = (int)cluster.block_rank();
     const int tid = threadIdx.x, nth = blockDim.x;
     const int Z = cd->Z, mb = cd->mb, nb = cd->nb, nnz = cd->nnz;
-    const float X = a.X, Xb = a.X * kSLog2e, Pb = s_psi_in<false>(a.X);  // X, X log2 e, phi(X) log2 e
+    const float Xb = a.X * kSLog2e, Pb = s_phi_b2(a.X);  // the clamp [phi(X), X] in base-2 units
 
     // bookkeeping: [0] bad flags (2, alternating by round), [2] the codeword being decoded
     // (int64 at 8: request << 32 | request-local index, -1 when the work is done)
@@ -393,7 +335,7 @@ __global__ void __cluster_dims__(CLUSTER_CTAS, 1, 1) __launch_bounds__(cl_thread
                 const int b0 = t_rowptr[l];
                 const uint32_t par = cl_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0,
                                                                       R + (b0 - blk0) * Z + r, app_0, app_1, r, Z,
-                                                                      X, Xb, Pb);
+                                                                      Xb, Pb);
                 pbad |= (par & kSign) != 0;
             };
             for (int r = p0; works && r < Z; r += ps)

@@ -8,8 +8,8 @@
 // of a QC block row touch disjoint variables) and column r of every block column of slot c.
 //
 // One round of the CTA (Sec. II two-phase message passing, Algorithm 1 loop order):
-//   check-node phase   every busy slot: Q = APP - R, R' from the phi rule (k_flood_cn's
-//                      arithmetic), written in place; the parity of the hard decisions
+//   check-node phase   every busy slot: Q = APP - R, R' from the check rule in the product
+//                      (tanh) domain (slot_common.cuh), written in place; the parity of the hard decisions
 //                      (APP sign bits) over each check marks a slot whose previous
 //                      iteration left an unsatisfied check
 //   barrier
@@ -72,20 +72,20 @@ struct FloodMultiArgs {
 template <int D, int DMAX, int V, typename MsgT>
 __device__ __forceinline__ void cn_rows(const int32_t *t_rord, const int32_t *t_dbeg, const int32_t *t_rowptr,
                                         const int4 *__restrict__ t_ed, const char *Ar, char *Rr, int r, int ZA,
-                                        int ZR, float X, float Xb, float Pb, uint32_t (&pbad)[V], int w0, int W)
+                                        int ZR, float Xb, float Pb, uint32_t (&pbad)[V], int w0, int W)
 {
     if constexpr (D <= 8) {
         if constexpr (D <= DMAX) {
             const int i1 = t_dbeg[D - 1];
             for (int i = t_dbeg[D - 2] + w0; i < i1; i += W)
-                slot_check_v<D, true, V, MsgT>(D, t_ed + t_rowptr[t_rord[i]], Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
+                slot_check_v<D, true, V, MsgT>(D, t_ed + t_rowptr[t_rord[i]], Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
         }
-        cn_rows<D + 1, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad, w0, W);
+        cn_rows<D + 1, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad, w0, W);
     } else if constexpr (DMAX > 8) {
         const int i1 = t_dbeg[8];
         for (int i = t_dbeg[7] + w0; i < i1; i += W) {
             const int l = t_rord[i], b0 = t_rowptr[l];
-            slot_check_dispatch<12, DMAX, V, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
+            slot_check_dispatch<12, DMAX, V, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
         }
     }
 }
@@ -137,7 +137,10 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
     float *APPs = reinterpret_cast<float *>(smem + slots_smem_head(a.tbl_ints));
 
     const int tid = threadIdx.x, nth = blockDim.x;
-    const float X = a.X, Xb = a.X * kSLog2e, Pb = s_psi_in<false>(a.X);  // X, X log2 e, phi(X) log2 e
+    const float Xb = a.X * kSLog2e, Pb = s_phi_b2(a.X);  // the clamp [phi(X), X] in base-2 units
+    // APP and R in base-2 units (LLR x log2 e) when kSlotB2: scaled at the refill and the
+    // variable-node sum, undone at the output
+    constexpr bool B2 = kSlotB2<MsgT>;
     constexpr uint32_t kSign = 0x80000000u;
     int grp = 0;
     {
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                 for (int u = 0; u < CH; u++)
                     if (j0 + u * W < nb) {
                         if (!isfinite(x[u])) atomicOr(cd->status, IN_NONFINITE);
-                        A[((j0 + u * W) * Z + r) * V + v] = x[u] + 0.0f;
+                        A[((j0 + u * W) * Z + r) * V + v] = B2 ? fmaf(x[u], kSLog2e, 0.0f) : x[u] + 0.0f;
                     }
             }
             for (int b = w0; b < nnz; b += W) {
@@ -293,13 +296,13 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
 #pragma unroll
                 for (int v = 0; v < V; v++) pbad[v] = 0;
                 if constexpr (DMAX == 8) {
-                    cn_rows<2, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad, w0, W);
+                    cn_rows<2, DMAX, V, MsgT>(t_rord, t_dbeg, t_rowptr, t_ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad, w0, W);
                 } else {
                     // codes with rows above degree 8: per-row dispatch in row order (measured
                     // faster here than the per-degree loops on the mixed-code launch)
                     for (int l = w0; l < mb; l += W) {
                         const int b0 = t_rowptr[l], dc = t_rowptr[l + 1] - b0;
-                        slot_check_dispatch<2, DMAX, V, MsgT>(dc, t_ed + b0, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
+                        slot_check_dispatch<2, DMAX, V, MsgT>(dc, t_ed + b0, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
                     }
                 }
 #pragma unroll
@@ -335,7 +338,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                         if (j < nb) {
                             float sacc[V];
 #pragma unroll
-                            for (int v = 0; v < V; v++) sacc[v] = lv[u][v];
+                            for (int v = 0; v < V; v++) sacc[v] = B2 ? lv[u][v] * kSLog2e : lv[u][v];
                             const int i0 = t_colptr[j];
                             vn_column<V, MsgT>(t_colptr[j + 1] - i0, t_colent + i0, Rr, sacc);
 #pragma unroll
@@ -358,7 +361,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                     for (int j = w0; j < nb; j += W) {
                         const float x = A[(j * Z + r) * V + v];
                         Bo[j * Z + r] = x < 0.0f ? 1 : 0;
-                        if (Ao) Ao[j * Z + r] = x;
+                        if (Ao) Ao[j * Z + r] = B2 ? x * kSLn2 : x;
                     }
                     if (lead) {
                         q.iters[cw[v]] = t[v];

@@ -16,7 +16,8 @@
 // Per check (the arithmetic of the flooding slot decoder, only the schedule differs):
 //   Q_k   = APP_n - R_k                                   over the check's edges
 //   R'_k  = prod_{other} sgn Q * min(X, phi( sum_{other} phi(clampX |Q|) ))
-//           (stored as fp16 when the messages are half precision)
+//           in the product (tanh) domain (slot_common.cuh), stored as fp16 when the
+//           messages are half precision
 //   APP_n = Q_k + R'_k   with R'_k the stored value, so that the next Q = APP - R removes
 //                        exactly what was added
 // After every full iteration each slot's hard decisions are checked against all of its
@@ -38,7 +39,7 @@ namespace ldpc {
 #endif
 
 // The FP32-message form keeps APP, Q and R in base-2 units (LLR x log2 e, set at the refill
-// and undone at the output), which spares the phi evaluations their scaling multiplies; the
+// and undone at the output), which spares the check rule its scaling multiplies; the
 // FP16-message form stays in natural units, so that its stored binary16 message is the
 // natural-unit value rounded, as the oracle's binary16 mode rounds it.
 template <typename MsgT>
@@ -87,18 +88,12 @@ struct MsgIO<__half> {
 // base (row r), with no wrap.
 __device__ __forceinline__ int lspa_app_off(const int4 d, int r, int ZA) { return d.x - (r >= d.z ? ZA : 0); }
 
-#ifndef LDPC_LSPA_TANH
-#define LDPC_LSPA_TANH 1  // product-domain check rule for rows of degree <= 8
-#endif
-
 // One check of row r (degree <= 8) in the product (tanh) domain: with d_k = e^-a_k,
 // a_k = |Q_k| clamped to [phi(X), X], the pair (alpha, beta) of the other edges' maps
 // (alpha, beta) <- (alpha + d beta, beta + d alpha) from (1, 0) gives
-// R'_k = ln(alpha / beta) = phi(sum_{other} phi(a)) (see slot_common.cuh); one ex2 and two
-// lg2 per edge.  In base-2 units (FP32 form) neither the ex2 argument nor the lg2
-// difference needs a scaling multiply.  The FP32 form holds Q per edge; the FP16 form
-// (1024 threads, 64 registers) forms it again from APP and R, neither of which is written
-// before its own edge is.
+// R'_k = ln(alpha / beta) = phi(sum_{other} phi(a)) (slot_common.cuh); one ex2 and two lg2
+// per edge.  The FP32 form holds Q per edge; the FP16 form (1024 threads, 64 registers)
+// forms it again from APP and R, neither of which is written before its own edge is.
 template <int D, bool EXACT, typename MsgT>
 __device__ __forceinline__ void layer_check_tanh(int dc, const int4 *__restrict__ ed, char *Ar, char *Rr, int r, int ZA,
                                                  float Xb, float Pb)
@@ -120,8 +115,7 @@ __device__ __forceinline__ void layer_check_tanh(int dc, const int4 *__restrict_
             const float qk = *at<float>(Ar, ao[k]) - MsgIO<MsgT>::ld(Rl + k * Zm);
             if constexpr (kHoldQ) q[k] = qk;
             sg ^= __float_as_uint(qk);
-            const float arg = B2 ? -fabsf(qk) : fabsf(qk) * -kSLog2e;
-            d[k] = s_ex2(fminf(fmaxf(arg, -Xb), -Pb));
+            d[k] = tanh_d<B2>(qk, Xb, Pb);
         }
     }
     float sa[D + 1], sb[D + 1];
@@ -148,8 +142,7 @@ __device__ __forceinline__ void layer_check_tanh(int dc, const int4 *__restrict_
             tanh_combine(pa, pb, sa[k + 1], sb[k + 1], al, be);
         }
         if (EXACT || k < dc) {
-            const float l = fminf(s_lg2(al) - s_lg2(be), Xb);
-            const float mag = B2 ? l : l * kSLn2;
+            const float mag = tanh_mag<B2>(al, be);
             float qk;
             if constexpr (kHoldQ)
                 qk = q[k];
@@ -169,17 +162,17 @@ __device__ __forceinline__ void layer_check_tanh(int dc, const int4 *__restrict_
 }
 
 // One check of row r in the layer whose blocks start at descriptor `ed`, computed from and
-// written back to the slot's APP (thread base Ar) and R (thread base Rr).
+// written back to the slot's APP (thread base Ar) and R (thread base Rr): rows up to degree 8
+// hold their state per edge, wider rows take the grouped form (see slot_common.cuh), with Q
+// formed from APP and R in both passes (neither is written before its own edge is) and
+// APP = Q + R' at the store.
 template <int D, bool EXACT, typename MsgT>
 __device__ __forceinline__ void layer_check(int dc, const int4 *__restrict__ ed, char *Ar, char *Rr, int r, int ZA,
-                                            float X, float Xb, float Pb)
+                                            float Xb, float Pb)
 {
-    if constexpr (LDPC_LSPA_TANH && D <= 8) {
+    if constexpr (D <= 8) {
         layer_check_tanh<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, Xb, Pb);
-        return;
-    } else if constexpr (LDPC_LSPA_TANH && D > 8) {
-        // rows above degree 8: the grouped rule, Q formed from APP and R in both passes
-        // (neither is written before its own edge is), APP = Q + R' at the store
+    } else {
         MsgT *Rl = at<MsgT>(Rr, ed[0].y);
         const int Zm = ZA / (int)sizeof(float);
         auto qof = [&](int k, bool) -> float {
@@ -189,104 +182,25 @@ __device__ __forceinline__ void layer_check(int dc, const int4 *__restrict__ ed,
             *at<float>(Ar, lspa_app_off(ed[k], r, ZA)) = q + MsgIO<MsgT>::st(Rl + k * Zm, m);
         };
         tanh_check_wide<D, kBase2<MsgT>>(dc, Xb, Pb, qof, put);
-        return;
-    }
-    constexpr uint32_t kSign = 0x80000000u;
-    // the layer's messages: row r of its blocks, one block (Z messages) apart
-    MsgT *Rl = at<MsgT>(Rr, ed[0].y);
-    const int Zm = ZA / (int)sizeof(float);
-    float a[D];                     // phi(clampX |Q|) in base-2 units, carrying the sign bit of Q
-    int ao[D <= 8 ? D : 1];         // byte offset of the edge's variable in APP
-    uint32_t sg = 0;
-    if constexpr (D <= 8 && sizeof(MsgT) == 4) {
-        float q[D];
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            if (EXACT || k < dc) {
-                const int4 d = ed[k];
-                ao[k] = lspa_app_off(d, r, ZA);
-                q[k] = *at<float>(Ar, ao[k]) - MsgIO<MsgT>::ld(Rl + k * Zm);
-                const uint32_t qs = __float_as_uint(q[k]) & kSign;
-                sg ^= qs;
-                a[k] = __uint_as_float(__float_as_uint(fminf(s_psi_in<kBase2<MsgT>>(fminf(fabsf(q[k]), X)), Xb)) | qs);
-            }
-        }
-        // exclusive sums from suffix and prefix sums (no cancellation)
-        float sf[D + 1];
-        sf[D] = 0.0f;
-#pragma unroll
-        for (int k = D - 1; k >= 0; k--) sf[k] = (EXACT || k < dc) ? sf[k + 1] + fabsf(a[k]) : 0.0f;
-        float pre = 0.0f;
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            if (EXACT || k < dc) {
-                const float mag = fminf(s_phi_out<kBase2<MsgT>>(pre + sf[k + 1]), X);
-                pre += fabsf(a[k]);
-                const float out = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(a[k]) ^ sg) & kSign));
-                *at<float>(Ar, ao[k]) = q[k] + MsgIO<MsgT>::st(Rl + k * Zm, out);
-            }
-        }
-    } else {
-        // fewer live registers: Q is not held per edge but formed again from APP and R
-        // (neither is written before its own edge is), and above degree 8 neither is the
-        // variable's index; exclusive sums as S - a_k, except for an edge holding more than
-        // half of S (at most one), whose sum of the others is formed directly
-        constexpr bool kHoldIdx = D <= 8;
-        float S = 0.0f, amax = 0.0f;
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            if (EXACT || k < dc) {
-                const int4 d = ed[k];
-                const int oa = lspa_app_off(d, r, ZA);
-                if constexpr (kHoldIdx) ao[k] = oa;
-                const float q = *at<float>(Ar, oa) - MsgIO<MsgT>::ld(Rl + k * Zm);
-                const uint32_t qs = __float_as_uint(q) & kSign;
-                sg ^= qs;
-                const float m = fminf(s_psi_in<kBase2<MsgT>>(fminf(fabsf(q), X)), Xb);
-                a[k] = __uint_as_float(__float_as_uint(m) | qs);
-                S += m;
-                amax = fmaxf(amax, m);
-            }
-        }
-        float o = 0.0f;
-#pragma unroll
-        for (int k = 0; k < D; k++)
-            if (EXACT || k < dc) o += (fabsf(a[k]) == amax) ? 0.0f : fabsf(a[k]);
-        const float sx = (amax > 0.5f * S) ? o : S - amax;
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            if (EXACT || k < dc) {
-                const float ak = fabsf(a[k]);
-                const float mag = fminf(s_phi_out<kBase2<MsgT>>(ak == amax ? sx : S - ak), X);
-                const float out = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(a[k]) ^ sg) & kSign));
-                int ai;
-                if constexpr (kHoldIdx)
-                    ai = ao[k];
-                else
-                    ai = lspa_app_off(ed[k], r, ZA);
-                const float q = *at<float>(Ar, ai) - MsgIO<MsgT>::ld(Rl + k * Zm);
-                *at<float>(Ar, ai) = q + MsgIO<MsgT>::st(Rl + k * Zm, out);
-            }
-        }
     }
 }
 
 template <int D, int DMAX, typename MsgT>
 __device__ __forceinline__ void layer_check_dispatch(int dc, const int4 *__restrict__ ed, char *Ar, char *Rr, int r,
-                                                     int ZA, float X, float Xb, float Pb)
+                                                     int ZA, float Xb, float Pb)
 {
     if constexpr (D >= DMAX) {
-        layer_check<DMAX, false, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb, Pb);
+        layer_check<DMAX, false, MsgT>(dc, ed, Ar, Rr, r, ZA, Xb, Pb);
     } else if constexpr (D <= 8) {
         if (dc == D)
-            layer_check<D, true, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb, Pb);
+            layer_check<D, true, MsgT>(dc, ed, Ar, Rr, r, ZA, Xb, Pb);
         else
-            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb, Pb);
+            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ed, Ar, Rr, r, ZA, Xb, Pb);
     } else {
         if (dc <= D)
-            layer_check<D, false, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb, Pb);
+            layer_check<D, false, MsgT>(dc, ed, Ar, Rr, r, ZA, Xb, Pb);
         else
-            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ed, Ar, Rr, r, ZA, X, Xb, Pb);
+            layer_check_dispatch<next_degree(D), DMAX, MsgT>(dc, ed, Ar, Rr, r, ZA, Xb, Pb);
     }
 }
 
@@ -357,9 +271,7 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
     MsgT *Rs = reinterpret_cast<MsgT *>(APPs + (size_t)C * a.strideA);
 
     const int tid = threadIdx.x, nth = blockDim.x;
-    // clamp X in the internal units (base-2 for FP32 messages); phi values are base-2 units
-    const float X = kBase2<MsgT> ? a.X * kSLog2e : a.X, Xb = a.X * kSLog2e;
-    const float Pb = s_psi_in<false>(a.X);  // phi(X) log2 e
+    const float Xb = a.X * kSLog2e, Pb = s_phi_b2(a.X);  // the clamp [phi(X), X] in base-2 units
     for (int i = tid; i < nnz; i += nth) {
         const int e = cd->ent[i], sh = e & 0xffff;
         t_ed[i] = make_int4((int)sizeof(float) * ((e >> 16) * Z + sh), (int)sizeof(MsgT) * i * Z, Z - sh, 0);
@@ -424,7 +336,7 @@ __global__ void __launch_bounds__(lspa_threads_max<DMAX, MsgT>(), 1) k_layered_s
         for (int l = 0; l < mb; l++) {
             if (busy) {
                 const int b0 = t_rowptr[l];
-                layer_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0, Ar, Rr, r, ZA, X, Xb, Pb);
+                layer_check_dispatch<2, DMAX, MsgT>(t_rowptr[l + 1] - b0, t_ed + b0, Ar, Rr, r, ZA, Xb, Pb);
             }
             group_sync(g, TPG);
         }

@@ -1,15 +1,14 @@
-// Device code shared by the slot decoders: phi in the two specialised forms, shared-memory
-// message access for one or two codewords per thread, and the degree-dispatched
-// check-node update of one check row.
+// Device code shared by the decoders that keep a codeword on chip (flooding slots, two-SM
+// clusters, layered sum-product): the check rule in the product (tanh) domain, shared-memory
+// message access for one or two codewords per thread, and the degree-dispatched check-node
+// update of one check row.
 #pragma once
 
 #include "ldpc_internal.h"
 
 namespace ldpc {
 
-// The approximate base-2 exponential and logarithm of the special-function units; phi
-// below is built from them in the two specialised forms of the streaming kernels (see
-// flood_kernels.cu).
+// The approximate base-2 exponential and logarithm of the special-function units.
 __device__ __forceinline__ float s_ex2(float x)
 {
     float y;
@@ -25,40 +24,13 @@ __device__ __forceinline__ float s_lg2(float x)
 constexpr float kSLog2e = 1.4426950408889634f;
 constexpr float kSLn2 = 0.6931471805599453f;
 
-// The phi evaluations below take their argument in natural units, or in base-2 units
-// (LLR x log2 e) for a decoder that keeps APP, Q and R scaled (B2), where neither needs a
-// scaling multiply.
-
-// phi(x), returned in base-2 units, of x = |Q| (already clamped) given in base-2 units (B2)
-// or in natural units.  ln((1 + t)/(1 - t)) is evaluated as lg2(1 + t) - lg2(1 - t): the two logarithms
-// are independent (a shorter dependency chain than a reciprocal followed by one logarithm)
-// and have opposite signs, so their difference does not cancel; for x above 3 (natural)
-// the series 2t + 2t^3/3 keeps the relative accuracy that the difference would lose.
-template <bool B2>
-__device__ __forceinline__ float s_psi_in(float x)
+// phi(X) log2 e, the lower end [phi(X), X] of the clamp of |Q| in base-2 units (once per
+// kernel): log2((1 + t)/(1 - t)) with t = e^-X, as two logarithms of opposite sign below
+// X = 3 and from the series 2t + 2t^3/3 (relative accuracy) above.
+__device__ __forceinline__ float s_phi_b2(float X)
 {
-    const float t = s_ex2(B2 ? -x : -x * kSLog2e);
-    const float big = t * fmaf(t * t, (2.0f / 3.0f) * kSLog2e, 2.0f * kSLog2e);
-    const float mid = s_lg2(1.0f + t) - s_lg2(1.0f - t);
-    return x > (B2 ? 4.328085f : 3.0f) ? big : mid;
-}
-
-// phi of a sum s2 given in base-2 units, returned in base-2 units (B2) or natural units.
-// 1 - e^-S is taken from its series below S = 1/16 (natural), where the difference would
-// cancel; in base-2 units the series coefficients carry the powers of ln 2.
-template <bool B2>
-__device__ __forceinline__ float s_phi_out(float s2)
-{
-    const float t = s_ex2(-s2);
-    float den;
-    if constexpr (B2) {
-        den = s2 < 0.09016844f ? s2 * fmaf(s2, fmaf(s2, 0.05550411f, -0.2402265f), kSLn2) : 1.0f - t;
-        return s_lg2(1.0f + t) - s_lg2(den);
-    } else {
-        const float S = s2 * kSLn2;
-        den = S < 0.0625f ? S * fmaf(S, fmaf(S, 1.0f / 6.0f, -0.5f), 1.0f) : 1.0f - t;
-        return (s_lg2(1.0f + t) - s_lg2(den)) * kSLn2;
-    }
+    const float t = s_ex2(-X * kSLog2e);
+    return X > 3.0f ? t * fmaf(t * t, (2.0f / 3.0f) * kSLog2e, 2.0f * kSLog2e) : s_lg2(1.0f + t) - s_lg2(1.0f - t);
 }
 
 // V consecutive slots share each shared-memory element group: APP and R are laid out
@@ -108,8 +80,6 @@ struct SMsg<__half, 2> {
 // degrees share buckets of four (edges past the degree are skipped under a uniform guard).
 __host__ __device__ constexpr int next_degree(int d) { return d < 8 ? d + 1 : d + 4; }
 
-// One check of row r for V slots: Q = APP - R over its edges, phi rule, messages written
-// in place (at the variable's position), parity of the APP sign bits accumulated in pbad.
 // Edge descriptors of one check row (built once per code when a CTA loads its tables): for
 // edge k of block b = (row l, column j, shift s), .x = byte offset of the posterior
 // (j*Z + s) and .y of the message (b*Z + s), both scaled by the element size and V, and
@@ -129,244 +99,45 @@ __device__ __forceinline__ const T *at(const char *base, int off) { return reint
 template <typename T>
 __device__ __forceinline__ T *at(char *base, int off) { return reinterpret_cast<T *>(base + off); }
 
-template <int D, bool EXACT, int V, typename MsgT>
-__device__ __forceinline__ void slot_check(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr, int r,
-                                           int ZA, int ZR, float X, float Xb, float Pb, uint32_t (&pbad)[V])
-{
-    constexpr uint32_t kSign = 0x80000000u;
-    float av[D][V];
-    int xo[D];
-    uint32_t sg[V], par[V];
-#pragma unroll
-    for (int v = 0; v < V; v++) sg[v] = par[v] = 0;
-#pragma unroll
-    for (int k = 0; k < D; k++) {
-        if (EXACT || k < dc) {
-            const EdgeRef e = edge_ref(ed[k], r, ZA, ZR);
-            xo[k] = e.orr;
-            float ap[V], rv[V];
-            SMsg<float, V>::ld(at<float>(Ar, e.oa), ap);
-            SMsg<MsgT, V>::ld(at<MsgT>(Rr, e.orr), rv);
-#pragma unroll
-            for (int v = 0; v < V; v++) {
-                const float q = ap[v] - rv[v];
-                par[v] ^= __float_as_uint(ap[v]);
-                const float mag = fminf(s_psi_in<false>(fminf(fabsf(q), X)), Xb);
-                const uint32_t qs = __float_as_uint(q) & kSign;
-                sg[v] ^= qs;
-                av[k][v] = __uint_as_float(__float_as_uint(mag) | qs);
-            }
-        }
-    }
-    if constexpr (D <= 8) {
-        // exclusive sums from suffix and prefix sums of |a| (no cancellation)
-        float sf[D + 1][V];
-#pragma unroll
-        for (int v = 0; v < V; v++) sf[D][v] = 0.0f;
-#pragma unroll
-        for (int k = D - 1; k >= 0; k--)
-#pragma unroll
-            for (int v = 0; v < V; v++) sf[k][v] = (EXACT || k < dc) ? sf[k + 1][v] + fabsf(av[k][v]) : 0.0f;
-        float pre[V];
-#pragma unroll
-        for (int v = 0; v < V; v++) pre[v] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            if (EXACT || k < dc) {
-                float out[V];
-#pragma unroll
-                for (int v = 0; v < V; v++) {
-                    const float mag = fminf(s_phi_out<false>(pre[v] + sf[k + 1][v]), X);
-                    pre[v] += fabsf(av[k][v]);
-                    out[v] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
-                }
-                SMsg<MsgT, V>::st(at<MsgT>(Rr, xo[k]), out);
-            }
-        }
-    } else {
-        // high degree: S - a_k, except for an edge holding more than half of S (at most one),
-        // whose sum of the others is formed directly - no per-edge suffix array to hold
-        float S[V], amax[V], sx[V];
-#pragma unroll
-        for (int v = 0; v < V; v++) {
-            S[v] = 0.0f;
-            amax[v] = 0.0f;
-        }
-#pragma unroll
-        for (int k = 0; k < D; k++)
-            if (EXACT || k < dc)
-#pragma unroll
-                for (int v = 0; v < V; v++) {
-                    S[v] += fabsf(av[k][v]);
-                    amax[v] = fmaxf(amax[v], fabsf(av[k][v]));
-                }
-#pragma unroll
-        for (int v = 0; v < V; v++) {
-            float o = 0.0f;
-#pragma unroll
-            for (int k = 0; k < D; k++)
-                if (EXACT || k < dc) o += (fabsf(av[k][v]) == amax[v]) ? 0.0f : fabsf(av[k][v]);
-            sx[v] = (amax[v] > 0.5f * S[v]) ? o : S[v] - amax[v];
-        }
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            if (EXACT || k < dc) {
-                float out[V];
-#pragma unroll
-                for (int v = 0; v < V; v++) {
-                    const float ak = fabsf(av[k][v]);
-                    const float mag = fminf(s_phi_out<false>(ak == amax[v] ? sx[v] : S[v] - ak), X);
-                    out[v] = __uint_as_float(__float_as_uint(mag) | ((__float_as_uint(av[k][v]) ^ sg[v]) & kSign));
-                }
-                SMsg<MsgT, V>::st(at<MsgT>(Rr, xo[k]), out);
-            }
-        }
-    }
-#pragma unroll
-    for (int v = 0; v < V; v++) pbad[v] |= par[v];
-}
-
-// The same check for two codewords held as float2: the FP32 multiplies, adds and FMAs of
-// both phi evaluations and of the prefix / suffix sums issue as packed pairs (FMUL2, FADD2,
-// FFMA2 on sm_100+); the special functions, min/max, selects and sign-bit logic stay scalar.
+// Two floats as the operand of the packed FP32x2 instructions (FFMA2, FMUL2, FADD2).
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-template <bool B2>
-__device__ __forceinline__ float2 psi_in2(float2 x)
-{
-    float2 arg = f2(-x.x, -x.y);
-    if constexpr (!B2) arg = __fmul2_rn(x, f2(-kSLog2e, -kSLog2e));
-    const float2 t = f2(s_ex2(arg.x), s_ex2(arg.y));
-    const float2 big = __fmul2_rn(t, __ffma2_rn(__fmul2_rn(t, t), f2((2.0f / 3.0f) * kSLog2e, (2.0f / 3.0f) * kSLog2e),
-                                                f2(2.0f * kSLog2e, 2.0f * kSLog2e)));
-    const float2 num = __fadd2_rn(t, f2(1.0f, 1.0f));
-    const float2 den = __ffma2_rn(t, f2(-1.0f, -1.0f), f2(1.0f, 1.0f));
-    const float2 mid = __fadd2_rn(f2(s_lg2(num.x), s_lg2(num.y)), f2(-s_lg2(den.x), -s_lg2(den.y)));
-    constexpr float th = B2 ? 4.328085f : 3.0f;
-    return f2(x.x > th ? big.x : mid.x, x.y > th ? big.y : mid.y);
-}
-
-template <bool B2>
-__device__ __forceinline__ float2 phi_out2(float2 s2)
-{
-    const float2 t = f2(s_ex2(-s2.x), s_ex2(-s2.y));
-    const float2 omt = __ffma2_rn(t, f2(-1.0f, -1.0f), f2(1.0f, 1.0f));
-    const float2 num = __fadd2_rn(t, f2(1.0f, 1.0f));
-    if constexpr (B2) {
-        const float2 poly = __fmul2_rn(
-            s2, __ffma2_rn(s2, __ffma2_rn(s2, f2(0.05550411f, 0.05550411f), f2(-0.2402265f, -0.2402265f)),
-                           f2(kSLn2, kSLn2)));
-        const float2 den = f2(s2.x < 0.09016844f ? poly.x : omt.x, s2.y < 0.09016844f ? poly.y : omt.y);
-        return __fadd2_rn(f2(s_lg2(num.x), s_lg2(num.y)), f2(-s_lg2(den.x), -s_lg2(den.y)));
-    } else {
-        const float2 S = __fmul2_rn(s2, f2(kSLn2, kSLn2));
-        const float2 poly = __fmul2_rn(S, __ffma2_rn(S, __ffma2_rn(S, f2(1.0f / 6.0f, 1.0f / 6.0f), f2(-0.5f, -0.5f)),
-                                                     f2(1.0f, 1.0f)));
-        const float2 den = f2(S.x < 0.0625f ? poly.x : omt.x, S.y < 0.0625f ? poly.y : omt.y);
-        const float2 d = __fadd2_rn(f2(s_lg2(num.x), s_lg2(num.y)), f2(-s_lg2(den.x), -s_lg2(den.y)));
-        return __fmul2_rn(d, f2(kSLn2, kSLn2));
-    }
-}
-
-template <int D, bool EXACT, typename MsgT>
-__device__ __forceinline__ void slot_check_pair(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr, int r,
-                                                int ZA, int ZR, float X, float Xb, float Pb, uint32_t (&pbad)[2])
-{
-    constexpr uint32_t kSign = 0x80000000u;
-    float2 av[D];
-    int xo[D];
-    uint32_t sg0 = 0, sg1 = 0, par0 = 0, par1 = 0;
-#pragma unroll
-    for (int k = 0; k < D; k++) {
-        if (EXACT || k < dc) {
-            const EdgeRef e = edge_ref(ed[k], r, ZA, ZR);
-            xo[k] = e.orr;
-            float ap[2], rv[2];
-            SMsg<float, 2>::ld(at<float>(Ar, e.oa), ap);
-            SMsg<MsgT, 2>::ld(at<MsgT>(Rr, e.orr), rv);
-            const float2 q = __ffma2_rn(f2(rv[0], rv[1]), f2(-1.0f, -1.0f), f2(ap[0], ap[1]));
-            par0 ^= __float_as_uint(ap[0]);
-            par1 ^= __float_as_uint(ap[1]);
-            const float2 m = psi_in2<false>(f2(fminf(fabsf(q.x), X), fminf(fabsf(q.y), X)));
-            const uint32_t qs0 = __float_as_uint(q.x) & kSign, qs1 = __float_as_uint(q.y) & kSign;
-            sg0 ^= qs0;
-            sg1 ^= qs1;
-            av[k] = f2(__uint_as_float(__float_as_uint(fminf(m.x, Xb)) | qs0),
-                       __uint_as_float(__float_as_uint(fminf(m.y, Xb)) | qs1));
-        }
-    }
-    if constexpr (D <= 8) {
-        float2 sf[D + 1];
-        sf[D] = f2(0.0f, 0.0f);
-#pragma unroll
-        for (int k = D - 1; k >= 0; k--)
-            sf[k] = (EXACT || k < dc) ? __fadd2_rn(sf[k + 1], f2(fabsf(av[k].x), fabsf(av[k].y))) : f2(0.0f, 0.0f);
-        float2 pre = f2(0.0f, 0.0f);
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            if (EXACT || k < dc) {
-                const float2 mag = phi_out2<false>(__fadd2_rn(pre, sf[k + 1]));
-                const float2 aa = f2(fabsf(av[k].x), fabsf(av[k].y));
-                pre = __fadd2_rn(pre, aa);
-                float out[2];
-                out[0] = __uint_as_float(__float_as_uint(fminf(mag.x, X)) | ((__float_as_uint(av[k].x) ^ sg0) & kSign));
-                out[1] = __uint_as_float(__float_as_uint(fminf(mag.y, X)) | ((__float_as_uint(av[k].y) ^ sg1) & kSign));
-                SMsg<MsgT, 2>::st(at<MsgT>(Rr, xo[k]), out);
-            }
-        }
-    } else {
-        // high degree: S - a_k with the dominant edge's sum formed directly (see slot_check)
-        float2 S = f2(0.0f, 0.0f);
-        float m0 = 0.0f, m1 = 0.0f;
-#pragma unroll
-        for (int k = 0; k < D; k++)
-            if (EXACT || k < dc) {
-                S = __fadd2_rn(S, f2(fabsf(av[k].x), fabsf(av[k].y)));
-                m0 = fmaxf(m0, fabsf(av[k].x));
-                m1 = fmaxf(m1, fabsf(av[k].y));
-            }
-        float o0 = 0.0f, o1 = 0.0f;
-#pragma unroll
-        for (int k = 0; k < D; k++)
-            if (EXACT || k < dc) {
-                o0 += (fabsf(av[k].x) == m0) ? 0.0f : fabsf(av[k].x);
-                o1 += (fabsf(av[k].y) == m1) ? 0.0f : fabsf(av[k].y);
-            }
-        const float x0 = (m0 > 0.5f * S.x) ? o0 : S.x - m0, x1 = (m1 > 0.5f * S.y) ? o1 : S.y - m1;
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            if (EXACT || k < dc) {
-                const float a0 = fabsf(av[k].x), a1 = fabsf(av[k].y);
-                const float2 mag = phi_out2<false>(f2(a0 == m0 ? x0 : S.x - a0, a1 == m1 ? x1 : S.y - a1));
-                float out[2];
-                out[0] = __uint_as_float(__float_as_uint(fminf(mag.x, X)) | ((__float_as_uint(av[k].x) ^ sg0) & kSign));
-                out[1] = __uint_as_float(__float_as_uint(fminf(mag.y, X)) | ((__float_as_uint(av[k].y) ^ sg1) & kSign));
-                SMsg<MsgT, 2>::st(at<MsgT>(Rr, xo[k]), out);
-            }
-        }
-    }
-    pbad[0] |= par0;
-    pbad[1] |= par1;
-}
-
-// The same check rule in the product (tanh) domain, rows of degree <= 8.  With
-// d_j = e^-a_j (a_j = min(|Q_j|, X)), tanh(a_j / 2) = (1 - d_j) / (1 + d_j); the exclusive
-// product P_k of the other edges' tanh gives R_k = ln((1 + P_k) / (1 - P_k)), which equals
-// phi(sum_{j != k} phi(a_j)) exactly (phi(x) = -ln tanh(x / 2) is its own inverse).
+// The check rule of the sum-product algorithm,
+//   R'_k = prod_{j != k} sgn Q_j * min(X, phi(sum_{j != k} phi(a_j))),  a_j = |Q_j| clamped to [phi(X), X],
+// in the product (tanh) domain.  With d_j = e^-a_j, tanh(a_j / 2) = (1 - d_j) / (1 + d_j), and
+// the exclusive product P_k of the other edges' tanh gives R_k = ln((1 + P_k) / (1 - P_k)),
+// which is phi(sum_{j != k} phi(a_j)) exactly (phi(x) = -ln tanh(x / 2) is its own inverse).
 // With B = prod (1 + d_j) and A = prod (1 - d_j), the pair alpha = (B + A) / 2,
 // beta = (B - A) / 2 gives (1 + P) / (1 - P) = alpha / beta, and one more factor d maps it
 // to (alpha + d beta, beta + d alpha): every term is non-negative, so neither 1 - P nor the
-// exclusion of edge k cancels (prefix and suffix pairs are combined as the product of the
-// two maps).  Per edge this is one ex2 and two lg2, against two of each phi evaluation
-// above, and no series branch.  The clamp of a_j to [phi(X), X] is a clamp of the ex2
-// argument to [-Xb, -Pb] (Xb = X log2 e, Pb = phi(X) log2 e).
+// exclusion of edge k cancels (the exclusion combines prefix and suffix pairs as the product
+// of the two maps).  Per edge this is one ex2 (of |Q|) and two lg2 (of alpha and beta).
+// The clamp of a_j to [phi(X), X] is a clamp of the ex2 argument to [-Xb, -Pb]
+// (Xb = X log2 e, Pb = phi(X) log2 e); the clamp min(X, .) of the result never binds, as
+// phi(sum_{j != k} phi(a_j)) <= min_{j != k} a_j <= X, so it is not applied.
+// B2: Q and R in base-2 units (LLR x log2 e), where neither the ex2 argument nor the lg2
+// difference needs a scaling multiply; else natural units (FP16 messages, whose stored value
+// is the natural one rounded to binary16).
+template <bool B2>
+__device__ __forceinline__ float tanh_d(float q, float Xb, float Pb)
+{
+    return s_ex2(fminf(fmaxf(B2 ? -fabsf(q) : fabsf(q) * -kSLog2e, -Xb), -Pb));
+}
+template <bool B2>
+__device__ __forceinline__ float tanh_mag(float al, float be)
+{
+    const float l = s_lg2(al) - s_lg2(be);
+    return B2 ? l : l * kSLn2;
+}
+
+// Rows up to degree 8, one codeword per thread: d and the sign held per edge.
 __device__ __forceinline__ void tanh_combine(float pa, float pb, float sa, float sb, float &al, float &be)
 {
     al = fmaf(pb, sb, pa * sa);
     be = fmaf(pb, sa, pa * sb);
 }
 
-template <int D, bool EXACT, typename MsgT>
+template <int D, bool EXACT, bool B2, typename MsgT>
 __device__ __forceinline__ void slot_check_tanh(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr, int r,
                                                 int ZA, int ZR, float Xb, float Pb, uint32_t (&pbad)[1])
 {
@@ -390,7 +161,7 @@ __device__ __forceinline__ void slot_check_tanh(int dc, const int4 *__restrict__
             par ^= __float_as_uint(ap[0]);
             qs[k] = __float_as_uint(q) & kSign;
             sg ^= qs[k];
-            d[k] = s_ex2(fminf(fmaxf(fabsf(q) * -kSLog2e, -Xb), -Pb));
+            d[k] = tanh_d<B2>(q, Xb, Pb);
         }
     }
     // suffix maps of edges k..D-1 applied to (1, 0)
@@ -418,8 +189,7 @@ __device__ __forceinline__ void slot_check_tanh(int dc, const int4 *__restrict__
             tanh_combine(pa, pb, sa[k + 1], sb[k + 1], al, be);
         }
         if (EXACT || k < dc) {
-            const float mag = fminf(s_lg2(al) - s_lg2(be), Xb) * kSLn2;
-            float out[1] = {__uint_as_float(__float_as_uint(mag) | (qs[k] ^ sg))};
+            float out[1] = {__uint_as_float(__float_as_uint(tanh_mag<B2>(al, be)) | (qs[k] ^ sg))};
             SMsg<MsgT, 1>::st(at<MsgT>(Rr, xo[k]), out);
         }
         if (k == 0) {
@@ -440,7 +210,7 @@ __device__ __forceinline__ void tanh_combine2(float2 pa, float2 pb, float2 sa, f
     be = __ffma2_rn(pb, sa, __fmul2_rn(pa, sb));
 }
 
-template <int D, bool EXACT, typename MsgT>
+template <int D, bool EXACT, bool B2, typename MsgT>
 __device__ __forceinline__ void slot_check_tanh_pair(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr,
                                                      int r, int ZA, int ZR, float Xb, float Pb,
                                                      uint32_t (&pbad)[2])
@@ -468,8 +238,7 @@ __device__ __forceinline__ void slot_check_tanh_pair(int dc, const int4 *__restr
             qs1[k] = __float_as_uint(q.y) & kSign;
             sg0 ^= qs0[k];
             sg1 ^= qs1[k];
-            d[k] = f2(s_ex2(fminf(fmaxf(fabsf(q.x) * -kSLog2e, -Xb), -Pb)),
-                      s_ex2(fminf(fmaxf(fabsf(q.y) * -kSLog2e, -Xb), -Pb)));
+            d[k] = f2(tanh_d<B2>(q.x, Xb, Pb), tanh_d<B2>(q.y, Xb, Pb));
         }
     }
     float2 sa[D + 1], sb[D + 1];
@@ -496,8 +265,8 @@ __device__ __forceinline__ void slot_check_tanh_pair(int dc, const int4 *__restr
             tanh_combine2(pa, pb, sa[k + 1], sb[k + 1], al, be);
         }
         if (EXACT || k < dc) {
-            const float2 l = __fadd2_rn(f2(s_lg2(al.x), s_lg2(al.y)), f2(-s_lg2(be.x), -s_lg2(be.y)));
-            const float2 mag = __fmul2_rn(f2(fminf(l.x, Xb), fminf(l.y, Xb)), f2(kSLn2, kSLn2));
+            float2 mag = __fadd2_rn(f2(s_lg2(al.x), s_lg2(al.y)), f2(-s_lg2(be.x), -s_lg2(be.y)));
+            if constexpr (!B2) mag = __fmul2_rn(mag, f2(kSLn2, kSLn2));
             float out[2] = {__uint_as_float(__float_as_uint(mag.x) | (qs0[k] ^ sg0)),
                             __uint_as_float(__float_as_uint(mag.y) | (qs1[k] ^ sg1))};
             SMsg<MsgT, 2>::st(at<MsgT>(Rr, xo[k]), out);
@@ -521,18 +290,11 @@ __device__ __forceinline__ void slot_check_tanh_pair(int dc, const int4 *__restr
 //   that starts from the product of the other groups' pairs.
 // Every term stays non-negative, as in the prefix / suffix form of rows up to degree 8.
 // qof(k, first) returns Q_k of edge k (`first`: pass 1, where the caller also takes what it
-// needs once per edge); put(k, R, Q) writes the signed message R of edge k (Q: its Q_k).  B2: Q and R in
-// base-2 units (LLR x log2 e), else natural units.
+// needs once per edge); put(k, R, Q) writes the signed message R of edge k (Q: its Q_k).
 __device__ __forceinline__ void pair_mul(float a1, float b1, float a2, float b2, float &a, float &b)
 {
     a = fmaf(b1, b2, a1 * a2);
     b = fmaf(b1, a2, a1 * b2);
-}
-
-template <bool B2>
-__device__ __forceinline__ float tanh_d(float q, float Xb, float Pb)
-{
-    return s_ex2(fminf(fmaxf(B2 ? -fabsf(q) : fabsf(q) * -kSLog2e, -Xb), -Pb));
 }
 
 template <int D, bool B2, typename QF, typename PF>
@@ -612,8 +374,7 @@ __device__ __forceinline__ void tanh_check_wide(int dc, float Xb, float Pb, QF q
             else
                 pair_mul(pa, pb, sa[i + 1], sb[i + 1], al, be);
             if (k < D && k < dc) {
-                const float l = fminf(s_lg2(al) - s_lg2(be), Xb);
-                const float mag = B2 ? l : l * kSLn2;
+                const float mag = tanh_mag<B2>(al, be);
                 put(k, __uint_as_float(__float_as_uint(mag) | ((qb[i] ^ sg) & kSign)), __uint_as_float(qb[i]));
             }
             if (i < 7) {
@@ -626,7 +387,7 @@ __device__ __forceinline__ void tanh_check_wide(int dc, float Xb, float Pb, QF q
 }
 
 // Flooding slot decoder, one codeword per thread, rows above degree 8.
-template <int D, typename MsgT>
+template <int D, bool B2, typename MsgT>
 __device__ __forceinline__ void slot_check_tanh_wide(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr,
                                                      int r, int ZA, int ZR, float Xb, float Pb, uint32_t (&pbad)[1])
 {
@@ -645,7 +406,7 @@ __device__ __forceinline__ void slot_check_tanh_wide(int dc, const int4 *__restr
         float out[1] = {m};
         SMsg<MsgT, 1>::st(at<MsgT>(Rr, e.orr), out);
     };
-    tanh_check_wide<D, false>(dc, Xb, Pb, qof, put);
+    tanh_check_wide<D, B2>(dc, Xb, Pb, qof, put);
     pbad[0] |= par;
 }
 
@@ -657,7 +418,7 @@ __device__ __forceinline__ void pair_mul2(float2 a1, float2 b1, float2 a2, float
     b = __ffma2_rn(b1, a2, __fmul2_rn(a1, b2));
 }
 
-template <int D, typename QF, typename PF>
+template <int D, bool B2, typename QF, typename PF>
 __device__ __forceinline__ void tanh_check_wide2(int dc, float Xb, float Pb, QF qof, PF put)
 {
     constexpr uint32_t kSign = 0x80000000u;
@@ -675,7 +436,7 @@ __device__ __forceinline__ void tanh_check_wide2(int dc, float Xb, float Pb, QF 
                 const float2 q = qof(k, true);
                 sg0 ^= __float_as_uint(q.x);
                 sg1 ^= __float_as_uint(q.y);
-                const float2 d = f2(tanh_d<false>(q.x, Xb, Pb), tanh_d<false>(q.y, Xb, Pb));
+                const float2 d = f2(tanh_d<B2>(q.x, Xb, Pb), tanh_d<B2>(q.y, Xb, Pb));
                 if (i == 0) {
                     gb[g] = d;
                 } else {
@@ -713,7 +474,7 @@ __device__ __forceinline__ void tanh_check_wide2(int dc, float Xb, float Pb, QF 
                 const float2 q = qof(k, false);
                 qb0[i] = __float_as_uint(q.x);
                 qb1[i] = __float_as_uint(q.y);
-                d[i] = f2(tanh_d<false>(q.x, Xb, Pb), tanh_d<false>(q.y, Xb, Pb));
+                d[i] = f2(tanh_d<B2>(q.x, Xb, Pb), tanh_d<B2>(q.y, Xb, Pb));
             }
         }
         float2 sa[9], sb[9];
@@ -735,8 +496,8 @@ __device__ __forceinline__ void tanh_check_wide2(int dc, float Xb, float Pb, QF 
             else
                 pair_mul2(pa, pb, sa[i + 1], sb[i + 1], al, be);
             if (k < D && k < dc) {
-                const float2 l = __fadd2_rn(f2(s_lg2(al.x), s_lg2(al.y)), f2(-s_lg2(be.x), -s_lg2(be.y)));
-                const float2 mag = __fmul2_rn(f2(fminf(l.x, Xb), fminf(l.y, Xb)), f2(kSLn2, kSLn2));
+                float2 mag = __fadd2_rn(f2(s_lg2(al.x), s_lg2(al.y)), f2(-s_lg2(be.x), -s_lg2(be.y)));
+                if constexpr (!B2) mag = __fmul2_rn(mag, f2(kSLn2, kSLn2));
                 put(k, f2(__uint_as_float(__float_as_uint(mag.x) | ((qb0[i] ^ sg0) & kSign)),
                           __uint_as_float(__float_as_uint(mag.y) | ((qb1[i] ^ sg1) & kSign))));
             }
@@ -750,7 +511,7 @@ __device__ __forceinline__ void tanh_check_wide2(int dc, float Xb, float Pb, QF 
 }
 
 // Flooding slot decoder, two codewords per thread, rows above degree 8.
-template <int D, typename MsgT>
+template <int D, bool B2, typename MsgT>
 __device__ __forceinline__ void slot_check_tanh_pair_wide(int dc, const int4 *__restrict__ ed, const char *Ar,
                                                           char *Rr, int r, int ZA, int ZR, float Xb, float Pb,
                                                           uint32_t (&pbad)[2])
@@ -772,55 +533,54 @@ __device__ __forceinline__ void slot_check_tanh_pair_wide(int dc, const int4 *__
         float out[2] = {m.x, m.y};
         SMsg<MsgT, 2>::st(at<MsgT>(Rr, e.orr), out);
     };
-    tanh_check_wide2<D>(dc, Xb, Pb, qof, put);
+    tanh_check_wide2<D, B2>(dc, Xb, Pb, qof, put);
     pbad[0] |= par0;
     pbad[1] |= par1;
 }
 
-#ifndef LDPC_SLOTS_TANH
-#define LDPC_SLOTS_TANH 1  // product-domain check rule for rows of degree <= 8
+// Whether the flooding slot decoder keeps APP and R in base-2 units with FP32 messages:
+// it saves two multiplies per edge update, yet measured slower on the 8192-codeword N = 1944
+// rate-1/2 sweep (6.34 against 6.50 info Gbit/s, same GPU), so natural units are the default.
+#ifndef LDPC_SLOTS_B2
+#define LDPC_SLOTS_B2 0
 #endif
-#ifndef LDPC_SLOTS_TANH_WIDE
-#define LDPC_SLOTS_TANH_WIDE 1  // and, in groups of 8 edges, for rows above degree 8
-#endif
+template <typename MsgT>
+constexpr bool kSlotB2 = LDPC_SLOTS_B2 && sizeof(MsgT) == 4;
 
-#ifndef LDPC_SLOTS_PAIRED_FP
-#define LDPC_SLOTS_PAIRED_FP 1  // packed FP32x2 arithmetic for two codewords per thread
-#endif
+// One check of row r for V slots (V codewords per thread): Q = APP - R over its edges, the
+// check rule, messages written in place (at the variable's position), parity of the APP sign
+// bits accumulated in pbad.
 template <int D, bool EXACT, int V, typename MsgT>
 __device__ __forceinline__ void slot_check_v(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr, int r,
-                                             int ZA, int ZR, float X, float Xb, float Pb, uint32_t (&pbad)[V])
+                                             int ZA, int ZR, float Xb, float Pb, uint32_t (&pbad)[V])
 {
-    if constexpr (LDPC_SLOTS_TANH && D <= 8 && V == 1)
-        slot_check_tanh<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
-    else if constexpr (LDPC_SLOTS_TANH_WIDE && D > 8 && V == 1)
-        slot_check_tanh_wide<D, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
-    else if constexpr (LDPC_SLOTS_TANH_WIDE && D > 8 && V == 2 && LDPC_SLOTS_PAIRED_FP)
-        slot_check_tanh_pair_wide<D, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
-    else if constexpr (LDPC_SLOTS_TANH && D <= 8 && V == 2 && LDPC_SLOTS_PAIRED_FP)
-        slot_check_tanh_pair<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
-    else if constexpr (V == 2 && LDPC_SLOTS_PAIRED_FP)
-        slot_check_pair<D, EXACT, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
+    constexpr bool B2 = kSlotB2<MsgT>;
+    if constexpr (D <= 8 && V == 1)
+        slot_check_tanh<D, EXACT, B2, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
+    else if constexpr (D <= 8)
+        slot_check_tanh_pair<D, EXACT, B2, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
+    else if constexpr (V == 1)
+        slot_check_tanh_wide<D, B2, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
     else
-        slot_check<D, EXACT, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
+        slot_check_tanh_pair_wide<D, B2, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
 }
 
 template <int D, int DMAX, int V, typename MsgT>
 __device__ __forceinline__ void slot_check_dispatch(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr,
-                                                    int r, int ZA, int ZR, float X, float Xb, float Pb, uint32_t (&pbad)[V])
+                                                    int r, int ZA, int ZR, float Xb, float Pb, uint32_t (&pbad)[V])
 {
     if constexpr (D >= DMAX) {
-        slot_check_v<DMAX, false, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
+        slot_check_v<DMAX, false, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
     } else if constexpr (D <= 8) {
         if (dc == D)
-            slot_check_v<D, true, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
+            slot_check_v<D, true, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
         else
-            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
+            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
     } else {
         if (dc <= D)
-            slot_check_v<D, false, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
+            slot_check_v<D, false, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
         else
-            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, X, Xb, Pb, pbad);
+            slot_check_dispatch<next_degree(D), DMAX, V, MsgT>(dc, ed, Ar, Rr, r, ZA, ZR, Xb, Pb, pbad);
     }
 }
 
