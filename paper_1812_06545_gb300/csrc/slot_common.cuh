@@ -308,10 +308,17 @@ __device__ __forceinline__ void tanh_check_wide(int dc, float Xb, float Pb, QF q
     for (int g = 0; g < G; g++) {
         ga[g] = 1.0f;
         gb[g] = 0.0f;
+    }
+    // the loops leave at the row's degree (a warp-uniform test) rather than predicate the
+    // edges of the body past it
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        if (8 * g >= dc) break;
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const int k = 8 * g + i;
-            if (k < D && k < dc) {
+            if (k >= D || k >= dc) break;
+            {
                 const float q = qof(k, true);
                 sg ^= __float_as_uint(q);
                 const float d = tanh_d<B2>(q, Xb, Pb);
@@ -346,10 +353,14 @@ __device__ __forceinline__ void tanh_check_wide(int dc, float Xb, float Pb, QF q
         uint32_t qb[8];
 #pragma unroll
         for (int i = 0; i < 8; i++) {
-            const int k = 8 * g + i;
-            d[i] = 0.0f;
+            d[i] = 0.0f;  // a missing edge is the identity map
             qb[i] = 0;
-            if (k < D && k < dc) {
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 8 * g + i;
+            if (k >= D || k >= dc) break;
+            {
                 const float q = qof(k, false);
                 qb[i] = __float_as_uint(q);
                 d[i] = tanh_d<B2>(q, Xb, Pb);
@@ -368,12 +379,13 @@ __device__ __forceinline__ void tanh_check_wide(int dc, float Xb, float Pb, QF q
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const int k = 8 * g + i;
+            if (k >= D || k >= dc) break;
             float al, be;
             if (i == 7)
                 al = pa, be = pb;
             else
                 pair_mul(pa, pb, sa[i + 1], sb[i + 1], al, be);
-            if (k < D && k < dc) {
+            {
                 const float mag = tanh_mag<B2>(al, be);
                 put(k, __uint_as_float(__float_as_uint(mag) | ((qb[i] ^ sg) & kSign)), __uint_as_float(qb[i]));
             }
@@ -429,10 +441,15 @@ __device__ __forceinline__ void tanh_check_wide2(int dc, float Xb, float Pb, QF 
     for (int g = 0; g < G; g++) {
         ga[g] = f2(1.0f, 1.0f);
         gb[g] = f2(0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        if (8 * g >= dc) break;
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const int k = 8 * g + i;
-            if (k < D && k < dc) {
+            if (k >= D || k >= dc) break;
+            {
                 const float2 q = qof(k, true);
                 sg0 ^= __float_as_uint(q.x);
                 sg1 ^= __float_as_uint(q.y);
@@ -467,10 +484,14 @@ __device__ __forceinline__ void tanh_check_wide2(int dc, float Xb, float Pb, QF 
         uint32_t qb0[8], qb1[8];
 #pragma unroll
         for (int i = 0; i < 8; i++) {
-            const int k = 8 * g + i;
             d[i] = f2(0.0f, 0.0f);
             qb0[i] = qb1[i] = 0;
-            if (k < D && k < dc) {
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 8 * g + i;
+            if (k >= D || k >= dc) break;
+            {
                 const float2 q = qof(k, false);
                 qb0[i] = __float_as_uint(q.x);
                 qb1[i] = __float_as_uint(q.y);
@@ -490,12 +511,13 @@ __device__ __forceinline__ void tanh_check_wide2(int dc, float Xb, float Pb, QF 
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const int k = 8 * g + i;
+            if (k >= D || k >= dc) break;
             float2 al, be;
             if (i == 7)
                 al = pa, be = pb;
             else
                 pair_mul2(pa, pb, sa[i + 1], sb[i + 1], al, be);
-            if (k < D && k < dc) {
+            {
                 float2 mag = __fadd2_rn(f2(s_lg2(al.x), s_lg2(al.y)), f2(-s_lg2(be.x), -s_lg2(be.y)));
                 if constexpr (!B2) mag = __fmul2_rn(mag, f2(kSLn2, kSLn2));
                 put(k, f2(__uint_as_float(__float_as_uint(mag.x) | ((qb0[i] ^ sg0) & kSign)),
