@@ -965,6 +965,7 @@ def main():
             "latency_ms": {"what": "one 8192-codeword decode call", "p50": float(np.percentile(lat, 50)),
                            "p99": float(np.percentile(lat, 99))},
             "avg_iterations": float(np.mean(np.concatenate(iters_np))), "fer": fer,
+            "edge_updates_per_batch": {f"{eb:.2f}": E * int(it.sum()) for eb, it in zip(w.ebn0_db, iters_np)},
             "coded_bit_iterations_per_s": world * args.steps * N * float(sum(int(it.sum()) for it in iters_np)) /
                                           (ms_max * 1e-3),
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
