@@ -93,6 +93,12 @@ __device__ __forceinline__ void cn_rows(const int32_t *t_rord, const int32_t *t_
 // Sum of the messages of one variable (column degree dv, message offsets ce) into sacc, in
 // the order of the column lists.  The common degrees get straight-line bodies; every lane
 // of a warp takes the same branch (a warp covers one block column).
+// (messages in base-2 units when kSlotB2: each is added as R ln 2)
+template <typename MsgT>
+__device__ __forceinline__ float vn_add(float s, float rv)
+{
+    return kSlotB2<MsgT> ? fmaf(rv, kSLn2, s) : s + rv;
+}
 template <int D, int V, typename MsgT>
 __device__ __forceinline__ void vn_sum(const int32_t *__restrict__ ce, const char *Rr, float (&sacc)[V])
 {
@@ -101,7 +107,7 @@ __device__ __forceinline__ void vn_sum(const int32_t *__restrict__ ce, const cha
         float rv[V];
         SMsg<MsgT, V>::ld(at<MsgT>(Rr, ce[k]), rv);
 #pragma unroll
-        for (int v = 0; v < V; v++) sacc[v] += rv[v];
+        for (int v = 0; v < V; v++) sacc[v] = vn_add<MsgT>(sacc[v], rv[v]);
     }
 }
 template <int V, typename MsgT>
@@ -118,7 +124,7 @@ __device__ __forceinline__ void vn_column(int dv, const int32_t *__restrict__ ce
             float rv[V];
             SMsg<MsgT, V>::ld(at<MsgT>(Rr, ce[i]), rv);
 #pragma unroll
-            for (int v = 0; v < V; v++) sacc[v] += rv[v];
+            for (int v = 0; v < V; v++) sacc[v] = vn_add<MsgT>(sacc[v], rv[v]);
         }
 }
 
@@ -138,9 +144,6 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
 
     const int tid = threadIdx.x, nth = blockDim.x;
     const float Xb = a.X * kSLog2e, Pb = s_phi_b2(a.X);  // the clamp [phi(X), X] in base-2 units
-    // APP and R in base-2 units (LLR x log2 e) when kSlotB2: scaled at the refill and the
-    // variable-node sum, undone at the output
-    constexpr bool B2 = kSlotB2<MsgT>;
     constexpr uint32_t kSign = 0x80000000u;
     int grp = 0;
     {
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                 for (int u = 0; u < CH; u++)
                     if (j0 + u * W < nb) {
                         if (!isfinite(x[u])) atomicOr(cd->status, IN_NONFINITE);
-                        A[((j0 + u * W) * Z + r) * V + v] = B2 ? fmaf(x[u], kSLog2e, 0.0f) : x[u] + 0.0f;
+                        A[((j0 + u * W) * Z + r) * V + v] = x[u] + 0.0f;
                     }
             }
             for (int b = w0; b < nnz; b += W) {
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                         if (j < nb) {
                             float sacc[V];
 #pragma unroll
-                            for (int v = 0; v < V; v++) sacc[v] = B2 ? lv[u][v] * kSLog2e : lv[u][v];
+                            for (int v = 0; v < V; v++) sacc[v] = lv[u][v];
                             const int i0 = t_colptr[j];
                             vn_column<V, MsgT>(t_colptr[j + 1] - i0, t_colent + i0, Rr, sacc);
 #pragma unroll
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(slot_threads_max<V>(), 1) k_flood_slots(const 
                     for (int j = w0; j < nb; j += W) {
                         const float x = A[(j * Z + r) * V + v];
                         Bo[j * Z + r] = x < 0.0f ? 1 : 0;
-                        if (Ao) Ao[j * Z + r] = B2 ? x * kSLn2 : x;
+                        if (Ao) Ao[j * Z + r] = x;
                     }
                     if (lead) {
                         q.iters[cw[v]] = t[v];

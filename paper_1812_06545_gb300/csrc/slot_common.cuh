@@ -157,7 +157,7 @@ __device__ __forceinline__ void slot_check_tanh(int dc, const int4 *__restrict__
             float ap[1], rv[1];
             SMsg<float, 1>::ld(at<float>(Ar, e.oa), ap);
             SMsg<MsgT, 1>::ld(at<MsgT>(Rr, e.orr), rv);
-            const float q = ap[0] - rv[0];
+            const float q = B2 ? fmaf(ap[0], kSLog2e, -rv[0]) : ap[0] - rv[0];
             par ^= __float_as_uint(ap[0]);
             qs[k] = __float_as_uint(q) & kSign;
             sg ^= qs[k];
@@ -231,7 +231,8 @@ __device__ __forceinline__ void slot_check_tanh_pair(int dc, const int4 *__restr
             float ap[2], rv[2];
             SMsg<float, 2>::ld(at<float>(Ar, e.oa), ap);
             SMsg<MsgT, 2>::ld(at<MsgT>(Rr, e.orr), rv);
-            const float2 q = __ffma2_rn(f2(rv[0], rv[1]), f2(-1.0f, -1.0f), f2(ap[0], ap[1]));
+            const float2 q = B2 ? __ffma2_rn(f2(ap[0], ap[1]), f2(kSLog2e, kSLog2e), f2(-rv[0], -rv[1]))
+                                : __ffma2_rn(f2(rv[0], rv[1]), f2(-1.0f, -1.0f), f2(ap[0], ap[1]));
             par0 ^= __float_as_uint(ap[0]);
             par1 ^= __float_as_uint(ap[1]);
             qs0[k] = __float_as_uint(q.x) & kSign;
@@ -410,7 +411,7 @@ __device__ __forceinline__ void slot_check_tanh_wide(int dc, const int4 *__restr
         SMsg<float, 1>::ld(at<float>(Ar, e.oa), ap);
         SMsg<MsgT, 1>::ld(at<MsgT>(Rr, e.orr), rv);
         if (first) par ^= __float_as_uint(ap[0]);
-        return ap[0] - rv[0];
+        return B2 ? fmaf(ap[0], kSLog2e, -rv[0]) : ap[0] - rv[0];
     };
     // the message offset is formed again at the store (holding it per edge costs D registers)
     auto put = [&](int k, float m, float) {
@@ -548,7 +549,8 @@ __device__ __forceinline__ void slot_check_tanh_pair_wide(int dc, const int4 *__
             par0 ^= __float_as_uint(ap[0]);
             par1 ^= __float_as_uint(ap[1]);
         }
-        return __ffma2_rn(f2(rv[0], rv[1]), f2(-1.0f, -1.0f), f2(ap[0], ap[1]));
+        return B2 ? __ffma2_rn(f2(ap[0], ap[1]), f2(kSLog2e, kSLog2e), f2(-rv[0], -rv[1]))
+                  : __ffma2_rn(f2(rv[0], rv[1]), f2(-1.0f, -1.0f), f2(ap[0], ap[1]));
     };
     auto put = [&](int k, float2 m) {
         const EdgeRef e = edge_ref(ed[k], r, ZA, ZR);
@@ -560,11 +562,13 @@ __device__ __forceinline__ void slot_check_tanh_pair_wide(int dc, const int4 *__
     pbad[1] |= par1;
 }
 
-// Whether the flooding slot decoder keeps APP and R in base-2 units with FP32 messages:
-// it saves two multiplies per edge update, yet measured slower on the 8192-codeword N = 1944
-// rate-1/2 sweep (6.34 against 6.50 info Gbit/s, same GPU), so natural units are the default.
+// Whether the flooding slot decoder stores FP32 messages in base-2 units (R log2 e) while
+// APP stays in natural units: Q in base-2 units is then one FMA (APP log2 e - R), the ex2
+// argument and the lg2 difference need no scaling multiply, and the variable-node sum
+// adds R ln 2 with an FMA; two multiplies fewer per edge update at no other cost.  (FP16
+// messages stay natural: the stored binary16 value is the natural one rounded.)
 #ifndef LDPC_SLOTS_B2
-#define LDPC_SLOTS_B2 0
+#define LDPC_SLOTS_B2 1
 #endif
 template <typename MsgT>
 constexpr bool kSlotB2 = LDPC_SLOTS_B2 && sizeof(MsgT) == 4;
