@@ -285,8 +285,8 @@ ldpc_status ldpc_profile_read(int32_t family, int64_t *launches, double *ms);
 ldpc_status ldpc_profile_reset(void);
 
 /* Measured special-function throughput of the current device in operations per second:
- * independent ex2.approx and lg2.approx chains on every SM (the units the phi evaluations
- * of the sum-product check rule run on).  Synchronizes `stream`; allocates 4 bytes. */
+ * independent ex2.approx and lg2.approx chains on every SM (the units the exponentials and
+ * logarithms of the sum-product check rule run on).  Synchronizes `stream`; allocates 4 bytes. */
 ldpc_status ldpc_sfu_throughput(double *ex2_per_s, double *lg2_per_s, void *stream);
 
 /* Device status word: the decoding kernels flag bad channel input without a host pass over
