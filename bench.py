@@ -494,7 +494,11 @@ def summary_line(line: dict, details_path: str) -> dict:
     rf = line["roofline"]
     out["roofline"] = {"bound": rf["bound"], "kernel": "k_flood_slots", "achieved": rf["achieved"],
                        "peak": rf["peak"], "unit": rf["unit"], "frac": rf["frac"], "traffic": rf["traffic"],
-                       "peak_source": "SFU rates measured live: 1/(1/ex2+2/lg2) edge updates/s"}
+                       "peak_source": "SFU rates measured live: 1/(1/ex2+2/lg2) edge updates/s (product-domain "
+                                      "check rule)"}
+    if rf.get("frac_of_phi_rule_ceiling") is not None:
+        # the same throughput against the ceiling of the phi-domain rule, 1/(2/ex2+4/lg2)
+        out["roofline"]["frac_of_phi_rule_ceiling"] = rf["frac_of_phi_rule_ceiling"]
     out["latency_ms"] = {"p50": line["latency_ms"]["p50"], "p99": line["latency_ms"]["p99"]}
     e2e = line["e2e"]
     out["e2e"] = {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "streams")}
@@ -934,6 +938,7 @@ def main():
     traffic = stored_traffic("k_flood_slots", SLOTS_SOURCES)
     roofline = {"bound": "alu", "kernel": "k_flood_slots (on-chip flooding slot decoder)", "achieved": achieved,
                 "peak": sfu_peak, "unit": "Gedge/s", "frac": (achieved / sfu_peak) if achieved else None,
+                "frac_of_phi_rule_ceiling": (achieved / sfu_peak_phi) if achieved else None,
                 "peak_source": (f"derived from the special-function throughput measured live on this GPU "
                                 f"(ex2 {ex2_s / 1e12:.2f} T/s = {ex2_s / n_sm / (sm_mhz * 1e6):.1f}/clk/SM, lg2 "
                                 f"{lg2_s / 1e12:.2f} T/s = {lg2_s / n_sm / (sm_mhz * 1e6):.1f}/clk/SM at {sm_mhz:.0f} MHz): "
