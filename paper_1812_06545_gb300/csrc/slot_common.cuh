@@ -399,6 +399,97 @@ __device__ __forceinline__ void tanh_check_wide(int dc, float Xb, float Pb, QF q
     }
 }
 
+// The grouped rule holding each edge's factor between its two passes (d_k in a register,
+// the sign of Q_k in d_k's own sign bit): pass 2 then needs no second load of the edge's
+// operands and no second ex2.  put(k, R) writes the signed message of edge k.
+template <int D, bool B2, typename QF, typename PF>
+__device__ __forceinline__ void tanh_check_wide_held(int dc, float Xb, float Pb, QF qof, PF put)
+{
+    constexpr uint32_t kSign = 0x80000000u;
+    constexpr int G = (D + 7) / 8;
+    float ga[G], gb[G];
+    uint32_t dq[D];  // d_k with the sign of Q_k
+    uint32_t sg = 0;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        ga[g] = 1.0f;
+        gb[g] = 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < D; k++) dq[k] = 0;
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        if (8 * g >= dc) break;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 8 * g + i;
+            if (k >= D || k >= dc) break;
+            const float q = qof(k);
+            const uint32_t qs = __float_as_uint(q) & kSign;
+            sg ^= qs;
+            const float d = tanh_d<B2>(q, Xb, Pb);
+            dq[k] = __float_as_uint(d) | qs;
+            if (i == 0) {
+                gb[g] = d;
+            } else {
+                const float t = fmaf(d, gb[g], ga[g]);
+                gb[g] = fmaf(d, ga[g], gb[g]);
+                ga[g] = t;
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        if (8 * g >= dc) break;
+        float pa = 1.0f, pb = 0.0f;
+        bool first = true;
+#pragma unroll
+        for (int h = 0; h < G; h++) {
+            if (h == g) continue;
+            if (first) {
+                pa = ga[h];
+                pb = gb[h];
+                first = false;
+            } else {
+                pair_mul(pa, pb, ga[h], gb[h], pa, pb);
+            }
+        }
+        float d[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) d[i] = (8 * g + i < D) ? __uint_as_float(dq[8 * g + i] & ~kSign) : 0.0f;
+        float sa[9], sb[9];
+        sa[8] = 1.0f;
+        sb[8] = 0.0f;
+        sa[7] = 1.0f;
+        sb[7] = d[7];
+#pragma unroll
+        for (int i = 6; i >= 1; i--) {
+            sa[i] = fmaf(d[i], sb[i + 1], sa[i + 1]);
+            sb[i] = fmaf(d[i], sa[i + 1], sb[i + 1]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            const int k = 8 * g + i;
+            if (k >= D || k >= dc) break;
+            float al, be;
+            if (i == 7)
+                al = pa, be = pb;
+            else
+                pair_mul(pa, pb, sa[i + 1], sb[i + 1], al, be);
+            put(k, __uint_as_float(__float_as_uint(tanh_mag<B2>(al, be)) | ((dq[k] ^ sg) & kSign)));
+            if (i < 7) {
+                const float t = fmaf(d[i], pb, pa);
+                pb = fmaf(d[i], pa, pb);
+                pa = t;
+            }
+        }
+    }
+}
+
+#ifndef LDPC_SLOTS_WIDE_HELD
+#define LDPC_SLOTS_WIDE_HELD 16  // widest row body (one codeword per thread) that holds its factors
+#endif
+
 // Flooding slot decoder, one codeword per thread, rows above degree 8.
 template <int D, bool B2, typename MsgT>
 __device__ __forceinline__ void slot_check_tanh_wide(int dc, const int4 *__restrict__ ed, const char *Ar, char *Rr,
@@ -419,7 +510,11 @@ __device__ __forceinline__ void slot_check_tanh_wide(int dc, const int4 *__restr
         float out[1] = {m};
         SMsg<MsgT, 1>::st(at<MsgT>(Rr, e.orr), out);
     };
-    tanh_check_wide<D, B2>(dc, Xb, Pb, qof, put);
+    if constexpr (D <= LDPC_SLOTS_WIDE_HELD)
+        tanh_check_wide_held<D, B2>(dc, Xb, Pb, [&](int k) { return qof(k, true); },
+                                    [&](int k, float m) { put(k, m, 0.0f); });
+    else
+        tanh_check_wide<D, B2>(dc, Xb, Pb, qof, put);
     pbad[0] |= par;
 }
 
