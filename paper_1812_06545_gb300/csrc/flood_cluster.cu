@@ -160,7 +160,11 @@ __device__ __forceinline__ uint32_t cl_check(int dc, const int4 *__restrict__ ed
             return ap - (float)Rr[k * Z];
         };
         auto put = [&](int k, float m, float) { Rr[k * Z] = MsgT(m); };
-        tanh_check_wide<D, false>(dc, Xb, Pb, qof, put);
+        if constexpr (D <= 12)  // hold the factors (no second remote load) where that does not spill
+            tanh_check_wide_held<D, false>(dc, Xb, Pb, [&](int k) { return qof(k, true); },
+                                           [&](int k, float m) { put(k, m, 0.0f); });
+        else
+            tanh_check_wide<D, false>(dc, Xb, Pb, qof, put);
         return par;
     }
 }
